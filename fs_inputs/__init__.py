@@ -1,0 +1,258 @@
+"""Seeded synthetic workloads for the folded-spectrum eigensolve.
+
+This module only draws random numbers and lays out the inputs of the
+plane-wave Hamiltonian: the orthorhombic cell, the FFT grid, the cutoff,
+Gaussian-well atoms, the local potential sampled on the grid, the Gaussian
+s/p projector set with its D matrices, the reference energy and the raw
+random start block.  It holds none of the eigensolver's arithmetic, so both
+the CPU oracle and the CUDA library can be fed from it.
+
+The paper (Sec. II, computational procedure) works on Cu nanowires with LDA
+and norm-conserving pseudopotentials, which are not available here; these
+Gaussian-well wires stand in for them.  Units are Hartree atomic units.
+
+Conventions shared by every consumer (stated, not computed, here):
+  * grid point j = (j0, j1, j2) sits at r_j = (j0 L0/n0, j1 L1/n1, j2 L2/n2);
+  * ``vloc`` is C-ordered [n0][n1][n2];
+  * a projector is (l, axis, width): l = 0 is an s Gaussian, l = 1 a p
+    Gaussian along Cartesian ``axis`` (0 = x, 1 = y, 2 = z);
+  * ``D`` is [natom][nproj][nproj], Hermitian (diagonal for these workloads);
+  * the cutoff is given in Hartree: a plane wave q = k + G is kept when
+    |q|^2 / 2 <= ecut.  The workload names quote the cutoff as a number X
+    which is read as Rydberg, so ecut = X / 2 (the only reading under which
+    each named grid holds its sphere).
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = ["Workload", "make_config", "make_box", "raw_start_block",
+           "gaussian_wells_on_grid", "CONFIG_NAMES"]
+
+CONFIG_NAMES = ("tiny", "wire", "longwire", "batched")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_EREF_FILE = os.path.join(os.path.dirname(_HERE), "tests", "golden", "eref.json")
+
+
+@dataclass
+class Workload:
+    name: str
+    L: np.ndarray            # (3,) cell lengths, bohr
+    n: tuple                 # grid (n0, n1, n2)
+    ecut: float              # Hartree
+    k: np.ndarray            # (3,) Cartesian k, 1/bohr
+    pos: np.ndarray          # (natom, 3) bohr
+    U: np.ndarray            # (natom,) well depths, Ha
+    w_v: float               # Gaussian width of the wells, bohr
+    proj: list               # [(l, axis, width)] per atom
+    D: np.ndarray            # (natom, nproj, nproj) Ha
+    vloc: np.ndarray         # (n0, n1, n2) float64, Ha
+    e_ref: float             # Ha
+    nstates: int
+    guard: int
+    seed: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def natom(self):
+        return int(self.pos.shape[0])
+
+    @property
+    def nproj(self):
+        return len(self.proj)
+
+    @property
+    def nbands(self):
+        return self.nstates + self.guard
+
+    def proj_arrays(self):
+        """(l[int32], axis[int32], width[float64]) arrays of the projector set."""
+        l = np.array([p[0] for p in self.proj], dtype=np.int32)
+        ax = np.array([p[1] for p in self.proj], dtype=np.int32)
+        w = np.array([p[2] for p in self.proj], dtype=np.float64)
+        return l, ax, w
+
+
+def default_guard(nstates: int) -> int:
+    return max(4, nstates // 16)
+
+
+def gaussian_wells_on_grid(L, n, pos, U, w_v):
+    """V(r_j) = -sum_a U_a sum_T exp(-|r_j - R_a - T|^2 / (2 w_v^2)).
+
+    The sum over lattice translations T is done by the minimum-image
+    displacement within a cut-off box of 9 w_v (the Gaussian is below 1e-17
+    beyond it), which is exact to that level for cells wider than 18 w_v and
+    otherwise falls back to the 27 neighbouring images.
+    """
+    L = np.asarray(L, dtype=np.float64)
+    n = tuple(int(v) for v in n)
+    V = np.zeros(n, dtype=np.float64)
+    rc = 9.0 * w_v
+    h = L / np.asarray(n)
+    if np.all(L > 2 * rc):
+        rad = np.ceil(rc / h).astype(int)
+        offs = [np.arange(-rad[d], rad[d] + 1) for d in range(3)]
+        for a in range(pos.shape[0]):
+            c = np.floor(pos[a] / h).astype(int)
+            idx = [c[d] + offs[d] for d in range(3)]
+            disp = [idx[d] * h[d] - pos[a, d] for d in range(3)]
+            r2 = (disp[0][:, None, None] ** 2 + disp[1][None, :, None] ** 2
+                  + disp[2][None, None, :] ** 2)
+            g = -U[a] * np.exp(-r2 / (2.0 * w_v * w_v))
+            ii = np.ix_(idx[0] % n[0], idx[1] % n[1], idx[2] % n[2])
+            np.add.at(V, ii, g)
+        return V
+    grids = np.meshgrid(*[np.arange(n[d]) * h[d] for d in range(3)], indexing="ij")
+    for a in range(pos.shape[0]):
+        for t0 in (-1, 0, 1):
+            for t1 in (-1, 0, 1):
+                for t2 in (-1, 0, 1):
+                    r2 = ((grids[0] - pos[a, 0] - t0 * L[0]) ** 2
+                          + (grids[1] - pos[a, 1] - t1 * L[1]) ** 2
+                          + (grids[2] - pos[a, 2] - t2 * L[2]) ** 2)
+                    V -= U[a] * np.exp(-r2 / (2.0 * w_v * w_v))
+    return V
+
+
+def _sp_set(widths):
+    out = []
+    for w in widths:
+        out.append((0, 0, float(w)))
+        for ax in range(3):
+            out.append((1, ax, float(w)))
+    return out
+
+
+def _load_eref():
+    try:
+        with open(_EREF_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _diag_D(rng, natom, nproj):
+    D = np.zeros((natom, nproj, nproj), dtype=np.float64)
+    d = rng.uniform(0.1, 0.5, size=(natom, nproj))
+    for a in range(natom):
+        D[a] = np.diag(d[a])
+    return D
+
+
+def _finish(name, L, n, ecut, k, pos, rng, proj, e_ref, nstates, seed,
+            w_v=1.0, guard=None, meta=None):
+    natom = pos.shape[0]
+    U = rng.uniform(1.0, 3.0, size=natom)
+    D = _diag_D(rng, natom, len(proj))
+    vloc = gaussian_wells_on_grid(L, n, pos, U, w_v)
+    if e_ref is None:
+        e_ref = float(_load_eref().get(name, {}).get("e_ref", -0.5 * float(np.mean(U))))
+    return Workload(name=name, L=np.asarray(L, np.float64), n=tuple(n), ecut=float(ecut),
+                    k=np.asarray(k, np.float64), pos=pos, U=U, w_v=w_v, proj=proj, D=D,
+                    vloc=vloc, e_ref=float(e_ref), nstates=int(nstates),
+                    guard=int(default_guard(nstates) if guard is None else guard),
+                    seed=int(seed), meta=meta or {})
+
+
+def make_config(name: str, seed: int | None = None, **over) -> Workload:
+    """The named workloads.
+
+    tiny     : 10x10x20 bohr, grid 16x16x32, cutoff 10 Ry, 2 fcc cells (a = 10)
+               stacked along z -> 8 wells, 4 projectors (s, p) of width 1.0,
+               8 states nearest 0.3 Ha.
+    wire     : 40x40x80 bohr, grid 72x72x144, cutoff 20 Ry, simple-cubic wire
+               4x4 cross-section x 16 layers (a = 5) -> 256 wells,
+               8 projectors (widths 0.8 and 1.2), 256 states.
+    longwire : 60x60x240 bohr, grid 108x108x432, cutoff 20 Ry, 5x5 x 40 layers
+               (a = 6) with 10 random vacancies -> 990 wells, 8 projectors,
+               512 states.
+    Every site is jittered by N(0, 0.1^2) per coordinate.
+    """
+    idx = {"tiny": 0, "wire": 1, "longwire": 2, "batched": 3}[name]
+    seed = 1907 + idx if seed is None else int(seed)
+    rng = np.random.default_rng(seed)
+    if name == "tiny":
+        a = 10.0
+        basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+        sites = np.concatenate([(basis + [0, 0, c]) * a for c in (0, 1)]) + a / 4
+        pos = sites + rng.normal(0.0, 0.1, size=sites.shape)
+        args = dict(L=(10.0, 10.0, 20.0), n=(16, 16, 32), ecut=5.0, k=(0, 0, 0),
+                    proj=_sp_set([1.0]), e_ref=0.3, nstates=8)
+    elif name == "wire":
+        a = 5.0
+        ii, jj, ll = np.meshgrid(np.arange(4), np.arange(4), np.arange(16), indexing="ij")
+        sites = np.stack([20.0 + (ii.ravel() - 1.5) * a, 20.0 + (jj.ravel() - 1.5) * a,
+                          (ll.ravel() + 0.5) * a], axis=1)
+        pos = sites + rng.normal(0.0, 0.1, size=sites.shape)
+        args = dict(L=(40.0, 40.0, 80.0), n=(72, 72, 144), ecut=10.0, k=(0, 0, 0),
+                    proj=_sp_set([0.8, 1.2]), e_ref=None, nstates=256)
+    elif name == "longwire":
+        a = 6.0
+        ii, jj, ll = np.meshgrid(np.arange(5), np.arange(5), np.arange(40), indexing="ij")
+        sites = np.stack([30.0 + (ii.ravel() - 2) * a, 30.0 + (jj.ravel() - 2) * a,
+                          (ll.ravel() + 0.5) * a], axis=1)
+        vac = rng.choice(sites.shape[0], size=10, replace=False)
+        sites = np.delete(sites, vac, axis=0)
+        pos = sites + rng.normal(0.0, 0.1, size=sites.shape)
+        args = dict(L=(60.0, 60.0, 240.0), n=(108, 108, 432), ecut=10.0, k=(0, 0, 0),
+                    proj=_sp_set([0.8, 1.2]), e_ref=None, nstates=512)
+    else:
+        raise ValueError("use make_batch() for the batched workload")
+    args.update(over)
+    return _finish(name, pos=pos, rng=rng, seed=seed, **args)
+
+
+def make_box(L=(10.0, 10.0, 20.0), n=(16, 16, 32), ecut=5.0, k=(0.0, 0.0, 0.0),
+             natom=4, widths=(1.0,), lattice=5.0, nstates=6, e_ref=0.3, seed=0,
+             jitter=0.1, guard=None, name="box") -> Workload:
+    """A small random box: ``natom`` jittered sites on a simple-cubic lattice
+    of spacing ``lattice`` centred in the cell; used for parity cases."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(L, dtype=np.float64)
+    side = int(np.ceil(natom ** (1.0 / 3.0)))
+    cand = np.array([[i, j, l] for i in range(side) for j in range(side) for l in range(side)],
+                    dtype=np.float64)[:natom]
+    sites = L / 2 + (cand - (side - 1) / 2.0) * lattice
+    pos = np.mod(sites + rng.normal(0.0, jitter, size=sites.shape), L)
+    return _finish(name, L=L, n=tuple(n), ecut=ecut, k=k, pos=pos, rng=rng,
+                   proj=_sp_set(widths) if widths else [], e_ref=e_ref, nstates=nstates,
+                   seed=seed, guard=guard)
+
+
+BATCH_GRIDS = ((32, 32, 32), (40, 40, 40), (48, 48, 48), (64, 64, 64), (48, 48, 96))
+
+
+def make_batch(nbox=96, seed=1910, spacing=0.5556):
+    """The batched-fragments workload: ``nbox`` independent boxes with grids
+    drawn from BATCH_GRIDS, cell = grid x spacing, cutoff 15 Ry, 8..64 wells on a
+    jittered simple-cubic lattice (a = 5), 4 projectors per atom, 32..128
+    states.  Each box's reference energy is minus half its mean well depth."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for b in range(nbox):
+        n = BATCH_GRIDS[int(rng.integers(0, len(BATCH_GRIDS)))]
+        L = np.asarray(n, dtype=np.float64) * spacing
+        natom = int(rng.integers(8, 65))
+        nst = int(rng.integers(32, 129))
+        w = make_box(L=L, n=n, ecut=7.5, natom=natom, widths=(1.0,), lattice=5.0,
+                     nstates=nst, e_ref=None, seed=int(rng.integers(0, 2**31)),
+                     name=f"batched{b}")
+        w.e_ref = -0.5 * float(np.mean(w.U))
+        out.append(w)
+    return out
+
+
+def raw_start_block(nbands: int, npw: int, seed: int) -> np.ndarray:
+    """Raw random start block: independent standard complex Gaussians
+    (real and imaginary parts N(0,1)), shape [nbands][npw], complex128.
+    The solver damps and orthonormalises it."""
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal((nbands, npw))
+    im = rng.standard_normal((nbands, npw))
+    return re + 1j * im
