@@ -1,0 +1,155 @@
+/*
+ * fs.h - C ABI of the GB300 folded-spectrum eigensolver.
+ *
+ * The library finds the eigenpairs of a plane-wave Kohn-Sham Hamiltonian H
+ * that lie nearest a reference energy E by minimising the folded operator
+ * A = (H - E)^2 (paper, Sec. II.C, Eq. wl1 and the folded-spectrum method it
+ * cites), using an all-band preconditioned conjugate-gradient method in its
+ * locally optimal block form with the paper's G-space diagonal preconditioner
+ * M(G) = 1/((G^2 - E)^2 + dE^2) (Sec. II.C, the definition under the M'
+ * equation), taken in Hartree as M(q) = 1/((|q|^2/2 - E)^2 + dE^2).
+ *
+ * Units: Hartree atomic units (bohr, Ha).
+ *
+ * H on the sphere S = { q = k + G : |q|^2/2 <= ecut } of plane waves
+ * G = 2 pi (g0/L0, g1/L1, g2/L2):
+ *   kinetic   |q|^2 / 2 on the diagonal;
+ *   local     Hloc[G,G'] = Vt((g - g') mod n), Vt = N^-1 sum_j V(r_j) e^{-2 pi i h.j/n},
+ *             applied as  FFT^-1 -> multiply by V(r) -> FFT  on the n0 x n1 x n2 grid;
+ *   nonlocal  sum_a sum_ij |beta_ai> D^a_ij <beta_aj| with Gaussian s/p projectors
+ *             beta_s(q)  = Omega^-1/2 (pi w^2)^{-3/4} (2 pi w^2)^{3/2} e^{-w^2 q^2/2} e^{-i q.R_a}
+ *             beta_p,x(q) = beta_s(q) (sqrt(2)/w) (-i w^2 q_x)   (and y, z).
+ *
+ * Sphere order: z-columns sorted by (g0, g1) ascending, each column by g2
+ * ascending.  Coefficient vectors are [nband][npw], complex interleaved
+ * (re, im): complex128 for FS_FP64, complex64 for FS_MIXED.
+ *
+ * Conventions:
+ *   - Every call returns fs_status; nothing throws across this boundary.
+ *   - fs_create copies every host input to the device; the caller keeps
+ *     ownership of its arrays and may free them on return.
+ *   - Device buffers passed in are caller-owned and must stay valid until
+ *     the call returns; all work runs on the context's stream and every call
+ *     returns only after that work has finished.
+ *   - A context is not thread-safe: one thread (one stream) per context.
+ *   - fs_last_error returns the message of the last failure on that context.
+ */
+#ifndef FS_H
+#define FS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fs_ctx fs_ctx;
+
+typedef enum {
+    FS_OK = 0,
+    FS_ERR_ARG = 1,             /* invalid argument (null pointer, size, range) */
+    FS_ERR_GRID_TOO_SMALL = 2,  /* some axis needs more than n_d distinct Miller indices */
+    FS_ERR_OOM = 3,             /* device allocation failed */
+    FS_ERR_CUDA = 4,            /* a CUDA runtime or library call failed */
+    FS_ERR_NUMERIC = 5,         /* NaN/Inf or a Gram matrix that is not positive definite */
+    FS_ERR_NOT_CONVERGED = 6,   /* iteration cap reached; results are still filled */
+    FS_ERR_TIMEOUT = 7,         /* a bounded device-side wait gave up */
+    FS_ERR_UNIMPLEMENTED = 8
+} fs_status;
+
+enum { FS_FP64 = 0, FS_MIXED = 1 };                     /* arithmetic of the vector work */
+enum { FS_PREC_M = 0, FS_PREC_TETER = 1, FS_PREC_LEARNED = 2 };
+enum { FS_HOST = 0, FS_DEVICE = 1 };                     /* where a state buffer lives */
+
+/* Orthorhombic cell (bohr) and FFT grid.  Grid point j sits at r_j = (j_d L_d / n_d). */
+typedef struct {
+    double L[3];
+    int n[3];
+} fs_grid;
+
+/* Gaussian s/p projectors, the same set on every atom.
+ *   pos   [natom][3]          atom positions, bohr
+ *   l     [nproj]             0 = s, 1 = p
+ *   axis  [nproj]             Cartesian axis of a p projector (0 = x, 1 = y, 2 = z); ignored for s
+ *   width [nproj]             Gaussian width w, bohr (exp(-r^2 / (2 w^2)))
+ *   D     [natom][nproj][nproj] real symmetric coupling, Ha
+ * natom = 0 or nproj = 0 means no nonlocal term. */
+typedef struct {
+    int natom;
+    int nproj;
+    const double* pos;
+    const int* l;
+    const int* axis;
+    const double* width;
+    const double* D;
+} fs_projectors;
+
+typedef struct {
+    int precision;             /* FS_FP64 or FS_MIXED */
+    int precond;               /* FS_PREC_M (default), FS_PREC_TETER, FS_PREC_LEARNED */
+    double dE;                 /* preconditioner broadening, Ha (default 0.5 when <= 0) */
+    int maxit;                 /* iteration cap (default 5000 when <= 0) */
+    int guard;                 /* extra bands beyond nstates (< 0: max(4, nstates/16)) */
+    unsigned long long seed;   /* start block when none is supplied */
+    void* cuda_stream;         /* cudaStream_t to run on (NULL: the library's own stream) */
+    int verbose;               /* > 0: one line per iteration on stderr */
+} fs_options;
+
+typedef struct {
+    int nconv;                 /* states among the nstates wanted with resid <= tol */
+    int iters;                 /* block iterations taken */
+    long long n_hpsi;          /* band applications of H (one per band per H call) */
+    double* eps;               /* caller-allocated [nstates]: eigenvalues, Ha, ordered by (|eps-E|, eps) */
+    double* resid;             /* caller-allocated [nstates]: ||H psi - eps psi|| (FP64) */
+    double seconds;            /* wall time of the solve */
+    int iters_mixed;           /* iterations taken in the mixed-precision stage */
+} fs_result;
+
+/* Build a context: enumerate the plane-wave sphere, upload V(r) and build the
+ * projector table.  vloc is host [n0][n1][n2] C-order, Ha.  k is Cartesian,
+ * 1/bohr.  opts may be NULL (defaults).  On failure *out is NULL and the status
+ * says why (FS_ERR_GRID_TOO_SMALL when 2 h_d + 1 > n_d on some axis). */
+fs_status fs_create(const fs_grid* grid, double ecut, const double k[3],
+                    const double* vloc, const fs_projectors* proj,
+                    const fs_options* opts, fs_ctx** out);
+
+/* Number of plane waves in the sphere. */
+fs_status fs_npw(const fs_ctx* ctx, int* npw);
+
+/* Miller indices of the sphere, host [npw][3] int, in sphere order. */
+fs_status fs_gvectors(const fs_ctx* ctx, int* miller);
+
+/* hpsi = (H - shift) psi for nband bands.  psi and hpsi are DEVICE pointers,
+ * [nband][npw] complex128 (precision FS_FP64) or complex64 (FS_MIXED); they
+ * must not overlap.  The local term runs through the fused column/plane FFT
+ * kernels, the nonlocal term through the projector contractions. */
+fs_status fs_apply_H(fs_ctx* ctx, const void* psi, void* hpsi, int nband,
+                     double shift, int precision);
+
+/* Supply the start block used by the next fs_solve: n bands, [n][npw]
+ * complex128, host or device (where = FS_HOST / FS_DEVICE).  damp = 1 scales
+ * each coefficient by 1/(1 + |q|^2/2) before use (raw random draws); damp = 0
+ * takes them as they are (warm start, e.g. from fs_get_states).  Bands beyond
+ * n are drawn from the seeded generator. */
+fs_status fs_set_initial_states(fs_ctx* ctx, const void* psi, int n, int damp, int where);
+
+/* Solve for the nstates eigenpairs nearest e_ref to residual tol (Ha).
+ * res->eps and res->resid must hold nstates doubles.  Returns
+ * FS_ERR_NOT_CONVERGED (results filled) when the cap is reached. */
+fs_status fs_solve(fs_ctx* ctx, double e_ref, int nstates, double tol, fs_result* res);
+
+/* Copy the n first states of the last solve (in the order of res->eps),
+ * [n][npw] complex128, to host or device memory. */
+fs_status fs_get_states(fs_ctx* ctx, void* psi, int n, int where);
+
+/* Release everything the context holds.  NULL is accepted. */
+void fs_destroy(fs_ctx* ctx);
+
+/* Message of the last failure on ctx ("" when none); static text when ctx is NULL. */
+const char* fs_last_error(const fs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FS_H */

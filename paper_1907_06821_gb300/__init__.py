@@ -1,0 +1,223 @@
+"""GB300 folded-spectrum eigensolver: Python binding of the C ABI in include/fs.h.
+
+This module only marshals arguments: every step of H application and of the
+solve runs in the CUDA library ``libfs_gb300.so`` built in-tree by
+``paper_1907_06821_gb300.build``.  PyTorch is used only to hold device
+memory.  There is no CPU fallback: if the library is missing the import of
+the binding fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfs_gb300.so")
+
+FS_OK, FS_ERR_ARG, FS_ERR_GRID_TOO_SMALL, FS_ERR_OOM, FS_ERR_CUDA, FS_ERR_NUMERIC, \
+    FS_ERR_NOT_CONVERGED, FS_ERR_TIMEOUT, FS_ERR_UNIMPLEMENTED = range(9)
+FS_FP64, FS_MIXED = 0, 1
+FS_PREC_M, FS_PREC_TETER, FS_PREC_LEARNED = 0, 1, 2
+FS_HOST, FS_DEVICE = 0, 1
+
+STATUS_NAMES = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_GRID_TOO_SMALL", 3: "FS_ERR_OOM",
+                4: "FS_ERR_CUDA", 5: "FS_ERR_NUMERIC", 6: "FS_ERR_NOT_CONVERGED",
+                7: "FS_ERR_TIMEOUT", 8: "FS_ERR_UNIMPLEMENTED"}
+
+
+class fs_grid(C.Structure):
+    _fields_ = [("L", C.c_double * 3), ("n", C.c_int * 3)]
+
+
+class fs_projectors(C.Structure):
+    _fields_ = [("natom", C.c_int), ("nproj", C.c_int), ("pos", C.POINTER(C.c_double)),
+                ("l", C.POINTER(C.c_int)), ("axis", C.POINTER(C.c_int)),
+                ("width", C.POINTER(C.c_double)), ("D", C.POINTER(C.c_double))]
+
+
+class fs_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("dE", C.c_double),
+                ("maxit", C.c_int), ("guard", C.c_int), ("seed", C.c_ulonglong),
+                ("cuda_stream", C.c_void_p), ("verbose", C.c_int)]
+
+
+class fs_result(C.Structure):
+    _fields_ = [("nconv", C.c_int), ("iters", C.c_int), ("n_hpsi", C.c_longlong),
+                ("eps", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
+                ("seconds", C.c_double), ("iters_mixed", C.c_int)]
+
+
+class FSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1907_06821_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, ip, dp = C.c_void_p, C.c_int, C.c_double
+    lib.fs_create.argtypes = [C.POINTER(fs_grid), dp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                              C.POINTER(fs_projectors), C.POINTER(fs_options), C.POINTER(vp)]
+    lib.fs_create.restype = ip
+    lib.fs_npw.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fs_npw.restype = ip
+    lib.fs_gvectors.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fs_gvectors.restype = ip
+    lib.fs_apply_H.argtypes = [vp, vp, vp, ip, dp, ip]
+    lib.fs_apply_H.restype = ip
+    lib.fs_set_initial_states.argtypes = [vp, vp, ip, ip, ip]
+    lib.fs_set_initial_states.restype = ip
+    lib.fs_solve.argtypes = [vp, dp, ip, dp, C.POINTER(fs_result)]
+    lib.fs_solve.restype = ip
+    lib.fs_get_states.argtypes = [vp, vp, ip, ip]
+    lib.fs_get_states.restype = ip
+    lib.fs_destroy.argtypes = [vp]
+    lib.fs_destroy.restype = None
+    lib.fs_last_error.argtypes = [vp]
+    lib.fs_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+class Context:
+    """One fs_ctx: a Hamiltonian on one plane-wave sphere.
+
+    Arguments mirror fs_create: cell ``L`` (bohr), grid ``n``, cutoff ``ecut``
+    (Ha), ``k`` (1/bohr), ``vloc`` [n0][n1][n2] (Ha), projector set
+    (``pos`` [natom][3], ``proj`` [(l, axis, width)], ``D`` [natom][np][np]).
+    """
+
+    def __init__(self, L, n, ecut, k, vloc, pos=None, proj=(), D=None, precision=FS_FP64,
+                 precond=FS_PREC_M, dE=0.5, maxit=5000, guard=-1, seed=1, stream=None, verbose=0):
+        self.lib = load_library()
+        self._keep = []
+        g = fs_grid((C.c_double * 3)(*[float(x) for x in L]), (C.c_int * 3)(*[int(x) for x in n]))
+        kk = np.ascontiguousarray(k, dtype=np.float64)
+        v = np.ascontiguousarray(vloc, dtype=np.float64)
+        if v.shape != tuple(int(x) for x in n):
+            raise ValueError("vloc shape does not match the grid")
+        pr = fs_projectors()
+        proj = list(proj)
+        if pos is not None and len(proj) > 0 and len(pos) > 0:
+            posa = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+            la = np.ascontiguousarray([p[0] for p in proj], dtype=np.int32)
+            axa = np.ascontiguousarray([p[1] for p in proj], dtype=np.int32)
+            wa = np.ascontiguousarray([p[2] for p in proj], dtype=np.float64)
+            Da = np.ascontiguousarray(D, dtype=np.float64).reshape(posa.shape[0], len(proj), len(proj))
+            self._keep += [posa, la, axa, wa, Da]
+            pr.natom, pr.nproj = posa.shape[0], len(proj)
+            pr.pos, pr.l, pr.axis, pr.width, pr.D = _dptr(posa), _iptr(la), _iptr(axa), _dptr(wa), _dptr(Da)
+        opt = fs_options(precision, precond, dE, maxit, guard, seed,
+                         C.c_void_p(stream) if stream else None, verbose)
+        self.precision = precision
+        h = C.c_void_p()
+        st = self.lib.fs_create(C.byref(g), float(ecut), _dptr(kk), _dptr(v), C.byref(pr), C.byref(opt),
+                                C.byref(h))
+        if st != FS_OK:
+            raise FSError(st, "fs_create failed")
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        """Build from an fs_inputs.Workload."""
+        return cls(w.L, w.n, w.ecut, w.k, w.vloc, pos=w.pos, proj=w.proj, D=w.D, **kw)
+
+    def _check(self, st, what):
+        if st != FS_OK:
+            msg = self.lib.fs_last_error(self.h)
+            raise FSError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    @property
+    def npw(self):
+        v = C.c_int()
+        self._check(self.lib.fs_npw(self.h, C.byref(v)), "fs_npw")
+        return v.value
+
+    def gvectors(self):
+        out = np.empty((self.npw, 3), dtype=np.int32)
+        self._check(self.lib.fs_gvectors(self.h, _iptr(out)), "fs_gvectors")
+        return out
+
+    def apply_H(self, psi, out=None, shift=0.0, precision=None):
+        """(H - shift) psi for a device tensor psi [nband][npw] (complex128 or complex64)."""
+        import torch
+        prec = FS_FP64 if psi.dtype == torch.complex128 else FS_MIXED
+        if precision is not None and precision != prec:
+            raise ValueError("tensor dtype does not match the requested precision")
+        if not psi.is_cuda or not psi.is_contiguous() or psi.dim() != 2 or psi.shape[1] != self.npw:
+            raise ValueError("psi must be a contiguous CUDA tensor [nband][npw]")
+        if out is None:
+            out = torch.empty_like(psi)
+        self._check(self.lib.fs_apply_H(self.h, C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr()),
+                                        psi.shape[0], float(shift), prec), "fs_apply_H")
+        return out
+
+    def set_initial_states(self, psi, damp=True):
+        """Start block [n][npw] complex128: a numpy array (host) or a CUDA tensor."""
+        if isinstance(psi, np.ndarray):
+            a = np.ascontiguousarray(psi, dtype=np.complex128)
+            self._check(self.lib.fs_set_initial_states(self.h, a.ctypes.data_as(C.c_void_p), a.shape[0],
+                                                       int(damp), FS_HOST), "fs_set_initial_states")
+        else:
+            self._check(self.lib.fs_set_initial_states(self.h, C.c_void_p(psi.data_ptr()), psi.shape[0],
+                                                       int(damp), FS_DEVICE), "fs_set_initial_states")
+
+    def solve(self, e_ref, nstates, tol=1e-6, allow_unconverged=False):
+        eps = np.zeros(nstates)
+        res = np.zeros(nstates)
+        r = fs_result()
+        r.eps = _dptr(eps)
+        r.resid = _dptr(res)
+        st = self.lib.fs_solve(self.h, float(e_ref), int(nstates), float(tol), C.byref(r))
+        if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
+            self._check(st, "fs_solve")
+        return dict(eps=eps, resid=res, nconv=r.nconv, iters=r.iters, iters_mixed=r.iters_mixed,
+                    n_hpsi=r.n_hpsi, seconds=r.seconds, status=st)
+
+    def get_states(self, n, device=False):
+        if device:
+            import torch
+            out = torch.empty((n, self.npw), dtype=torch.complex128, device="cuda")
+            self._check(self.lib.fs_get_states(self.h, C.c_void_p(out.data_ptr()), n, FS_DEVICE),
+                        "fs_get_states")
+            return out
+        out = np.empty((n, self.npw), dtype=np.complex128)
+        self._check(self.lib.fs_get_states(self.h, out.ctypes.data_as(C.c_void_p), n, FS_HOST),
+                    "fs_get_states")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,197 @@
+// Shared device helpers and the context layout of the folded-spectrum library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fs.h"
+
+// ------------------------------------------------------------------ complex
+template <typename R> struct cplx;
+template <> struct cplx<double> { using t = double2; };
+template <> struct cplx<float> { using t = float2; };
+
+__host__ __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+
+template <typename T2> __host__ __device__ __forceinline__ T2 cadd(T2 a, T2 b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T2> __host__ __device__ __forceinline__ T2 csub(T2 a, T2 b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T2> __host__ __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <typename T2> __host__ __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
+    return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+template <typename T2, typename R> __host__ __device__ __forceinline__ T2 cscale(T2 a, R s) {
+    return mk(a.x * s, a.y * s);
+}
+
+template <typename T2> struct real_of;
+template <> struct real_of<double2> { using t = double; };
+template <> struct real_of<float2> { using t = float; };
+
+__device__ __forceinline__ double2 to_c(double2 a, double2*) { return a; }
+__device__ __forceinline__ float2 to_c(double2 a, float2*) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ float2 to_c(float2 a, float2*) { return a; }
+__device__ __forceinline__ double2 to_c(float2 a, double2*) { return make_double2(a.x, a.y); }
+template <typename T2, typename S2> __device__ __forceinline__ T2 conv(S2 a) { return to_c(a, (T2*)nullptr); }
+
+// ------------------------------------------------------------------ FFT plan
+// A 1-D length-n transform as a list of radix-2/3/4/5 Stockham stages.
+// tw points to n twiddles w^p = exp(-2 pi i p / n) in the transform's precision.
+// group = how many lines the kernel's thread block transforms at once.
+#define FS_MAX_STAGES 12
+template <typename T2> struct FftPlan {
+    int n;
+    int nst;
+    int rad[FS_MAX_STAGES];
+    int group;
+    const T2* tw;
+};
+
+// ------------------------------------------------------------------ errors
+#define FS_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            throw fs_error(FS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                \
+    } while (0)
+
+#define FS_SOLVER(call)                                                                  \
+    do {                                                                                 \
+        cusolverStatus_t s_ = (call);                                                    \
+        if (s_ != CUSOLVER_STATUS_SUCCESS) {                                             \
+            throw fs_error(FS_ERR_CUDA, std::string(#call) + ": cusolver status " + std::to_string((int)s_)); \
+        }                                                                                \
+    } while (0)
+
+struct fs_error {
+    fs_status code;
+    std::string msg;
+    fs_error(fs_status c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+// ------------------------------------------------------------------ device buffer
+struct dbuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    void alloc(size_t nb) {
+        release();
+        if (nb == 0) return;
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            (void)cudaGetLastError();
+            throw fs_error(FS_ERR_OOM, "cudaMalloc of " + std::to_string(nb) + " bytes failed");
+        }
+        bytes = nb;
+    }
+    void ensure(size_t nb) {
+        if (nb > bytes) alloc(nb);
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+    ~dbuf() { release(); }
+    dbuf() = default;
+    dbuf(const dbuf&) = delete;
+    dbuf& operator=(const dbuf&) = delete;
+};
+
+// ------------------------------------------------------------------ context
+struct fs_ctx {
+    // geometry and basis
+    double L[3];
+    int n[3];
+    double ecut;
+    double k[3];
+    int npw = 0;
+    int ncol = 0;
+    int natom = 0, nproj = 0, nptot = 0;
+    std::vector<int> miller;      // [npw][3]
+    std::vector<double> kin_h;    // [npw]
+    fs_options opt;
+
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cusolverDnHandle_t solver = nullptr;
+
+    // basis tables (device)
+    dbuf col_start;   // int [ncol+1]
+    dbuf col_xy;      // int [ncol] : (g0 mod n0) * n1 + (g1 mod n1)
+    dbuf ent_col;     // int [npw]  : column of each sphere entry
+    dbuf ent_z;       // int [npw]  : g2 mod n2
+    dbuf kin;         // double [npw] : |k+G|^2 / 2
+    dbuf vz64;        // double [n2][n0*n1]
+    dbuf vz32;        // float  [n2][n0*n1]
+    dbuf tw64[3];     // double2 [n_d]
+    dbuf tw32[3];     // float2  [n_d]
+    FftPlan<double2> plan64[3];
+    FftPlan<float2> plan32[3];
+    int cpb = 16;     // columns per block in the column kernels
+
+    // projectors
+    dbuf beta64;      // double2 [nptot][npw]
+    dbuf beta32;      // float2  [nptot][npw]
+    dbuf Dmat;        // double  [natom][nproj][nproj]
+
+    // workspace for H application
+    dbuf colbuf;      // [nb][n2][ncol] complex
+    dbuf projbuf;     // [nb][nptot] complex (P)
+    dbuf projbuf2;    // [nb][nptot] complex (Q = D P)
+    dbuf splitk;      // split-K partial sums
+
+    // solver state
+    dbuf init_states; // double2 [ninit][npw]
+    int ninit = 0;
+    int init_damp = 1;
+    dbuf result_states;  // double2 [nstates][npw]
+    int nresult = 0;
+
+    std::string err;
+};
+
+// ------------------------------------------------------------------ internal entry points
+// H application (fs_h.cu)
+template <typename T2>
+void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, const int* rowmap_in = nullptr);
+
+void ctx_prepare_fft(fs_ctx* c);
+
+// GEMMs (fs_gemm.cu)
+// Gram form: C(i, j) = alpha * sum_k conj(A[ia(i)][k]) * B[ib(j)][k]  (+ beta * C(i, j))
+// A rows: M, stride lda; B rows: N, stride ldb; K contiguous.  Optional row maps.
+// C(i, j) is written as double2 at C[i * ci + j * cj].
+template <typename T2>
+void gemm_gram(fs_ctx* c, int M, int N, int K, const T2* A, long lda, const int* amap, const T2* B, long ldb,
+               const int* bmap, double2* C, long ci, long cj, double alpha, double beta);
+// Rotation/apply form: C[ic(i)][n] = alpha * sum_k Acoef(i, k) * B[ib(k)][n] + beta * D[ic(i)][n]
+// Acoef(i, k) = A[i * ai + k * ak] (A2 complex coefficients, double2 or T2);  D may equal C or be null.
+template <typename T2, typename A2>
+void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const T2* B, long ldb, const int* bmap,
+             T2* C, long ldc, const int* cmap, double alpha, double beta, const T2* D, long ldd);
+
+// vector kernels (fs_vec.cu)
+template <typename T2> void vec_resid(fs_ctx* c, const T2* X, const T2* Y, int m, double* resid, double2* dot);
+template <typename T2>
+void vec_make_w(fs_ctx* c, const T2* X, const T2* Z, const double* theta, const int* act, int na, T2* W, double e_ref,
+                double dE, int precond, const double* band_kin);
+template <typename T2> void vec_row_norms(fs_ctx* c, const T2* X, const int* map, int nrows, double* out);
+template <typename T2> void vec_scale_rows(fs_ctx* c, T2* X, const int* map, int nrows, const double* nrm);
+template <typename T2>
+void vec_resid_shift(fs_ctx* c, const T2* X, const T2* Y, const double* shift, int m, double* resid);
+void vec_damp_random(fs_ctx* c, double2* X, int m, int first, unsigned long long seed);
+void vec_damp(fs_ctx* c, double2* X, int m);
+template <typename S2, typename T2> void vec_convert(fs_ctx* c, const S2* in, T2* out, size_t count);
+
+// solver (fs_solver.cu)
+fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res);

@@ -1,0 +1,392 @@
+// Application of the plane-wave Hamiltonian: hpsi = (H - shift) psi.
+//
+// Local part (kinetic + V_loc), two-pass 3-D FFT decomposition:
+//   1. col_inverse : unpack each sphere z-column into a zero-filled line of
+//                    n2, inverse FFT along z, write to the column buffer
+//                    [band][z][column] (only the ncol columns that hold
+//                    plane waves exist; the rest of the grid is zero).
+//   2. plane       : per (band, z) plane: scatter the columns into an n0 x n1
+//                    plane in shared memory, inverse 2-D FFT, multiply by
+//                    V(r), forward 2-D FFT, gather the columns back.
+//   3. col_forward : forward FFT along z, scale by 1/N, pick the sphere
+//                    entries and add (|q|^2/2 - shift) psi.
+// Nonlocal part: P = B^H psi (Gram GEMM), Q = D P per atom, hpsi += B Q.
+#include "fs_common.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+// ------------------------------------------------------------------ radix butterflies
+// out[k] = sum_r v[r] exp(s * 2 pi i r k / R), s = +1 (inverse) or -1 (forward)
+template <typename T2> __device__ __forceinline__ T2 mul_si(T2 a, int s) {  // a * (s i)
+    return s > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
+}
+
+template <typename T2, int R> struct Bfly;
+
+template <typename T2> struct Bfly<T2, 2> {
+    __device__ __forceinline__ static void run(T2* v, int) {
+        T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <typename T2> struct Bfly<T2, 4> {
+    __device__ __forceinline__ static void run(T2* v, int s) {
+        T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        T2 t2 = cadd(v[1], v[3]), t3 = mul_si(csub(v[1], v[3]), s);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+
+template <typename T2> struct Bfly<T2, 3> {
+    __device__ __forceinline__ static void run(T2* v, int s) {
+        using R = typename real_of<T2>::t;
+        const R h = (R)0.86602540378443864676;  // sqrt(3)/2
+        T2 t = cadd(v[1], v[2]);
+        T2 d = mul_si(cscale(csub(v[1], v[2]), h), s);
+        T2 a = csub(v[0], cscale(t, (R)0.5));
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(a, d);
+        v[2] = csub(a, d);
+    }
+};
+
+template <typename T2> struct Bfly<T2, 5> {
+    __device__ __forceinline__ static void run(T2* v, int s) {
+        using R = typename real_of<T2>::t;
+        const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
+        const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;
+        T2 a14 = cadd(v[1], v[4]), d14 = csub(v[1], v[4]);
+        T2 a23 = cadd(v[2], v[3]), d23 = csub(v[2], v[3]);
+        T2 r1 = cadd(v[0], cadd(cscale(a14, c1), cscale(a23, c2)));
+        T2 r2 = cadd(v[0], cadd(cscale(a14, c2), cscale(a23, c1)));
+        T2 i1 = mul_si(cadd(cscale(d14, s1), cscale(d23, s2)), s);
+        T2 i2 = mul_si(csub(cscale(d14, s2), cscale(d23, s1)), s);
+        v[0] = cadd(v[0], cadd(a14, a23));
+        v[1] = cadd(r1, i1);
+        v[4] = csub(r1, i1);
+        v[2] = cadd(r2, i2);
+        v[3] = csub(r2, i2);
+    }
+};
+
+// One Stockham stage over `nl` lines of length n held in shared memory.
+// All reads of the stage are staged in registers before any write, so the
+// stage runs in place.  KM butterflies per thread must cover nl * n / R.
+template <typename T2, int R, int KM>
+__device__ __forceinline__ void fft_stage(T2* buf, int n, int nl, int lstride, int estride, int Ns,
+                                          const T2* __restrict__ tw, int sign) {
+    const int nb = n / R;
+    const int total = nb * nl;
+    T2 v[KM][R];
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) {
+        int t = threadIdx.x + kk * blockDim.x;
+        if (t < total) {
+            int line = t / nb, j = t - line * nb;
+            const T2* base = buf + (long)line * lstride;
+            int tj = j % Ns;
+            int step = (n / (Ns * R)) * tj;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                T2 x = base[(j + r * nb) * estride];
+                if (r > 0 && step > 0) {
+                    T2 w = __ldg(&tw[r * step]);
+                    if (sign > 0) w.y = -w.y;
+                    x = cmul(x, w);
+                }
+                v[kk][r] = x;
+            }
+            Bfly<T2, R>::run(v[kk], sign);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KM; ++kk) {
+        int t = threadIdx.x + kk * blockDim.x;
+        if (t < total) {
+            int line = t / nb, j = t - line * nb;
+            T2* base = buf + (long)line * lstride;
+            int tj = j % Ns;
+            int idxD = (j / Ns) * Ns * R + tj;
+#pragma unroll
+            for (int r = 0; r < R; ++r) base[(idxD + r * Ns) * estride] = v[kk][r];
+        }
+    }
+    __syncthreads();
+}
+
+// Transform nlines lines (groups of plan.group lines at a time); EPT = element budget per thread.
+template <typename T2, int EPT>
+__device__ void fft_lines(T2* buf, const FftPlan<T2>& p, int nlines, int lstride, int estride, int sign) {
+    for (int l0 = 0; l0 < nlines; l0 += p.group) {
+        int nl = min(p.group, nlines - l0);
+        T2* b = buf + (long)l0 * lstride;
+        int Ns = 1;
+        for (int s = 0; s < p.nst; ++s) {
+            int R = p.rad[s];
+            if (R == 4)
+                fft_stage<T2, 4, (EPT + 3) / 4>(b, p.n, nl, lstride, estride, Ns, p.tw, sign);
+            else if (R == 2)
+                fft_stage<T2, 2, (EPT + 1) / 2>(b, p.n, nl, lstride, estride, Ns, p.tw, sign);
+            else if (R == 3)
+                fft_stage<T2, 3, (EPT + 2) / 3>(b, p.n, nl, lstride, estride, Ns, p.tw, sign);
+            else
+                fft_stage<T2, 5, (EPT + 4) / 5>(b, p.n, nl, lstride, estride, Ns, p.tw, sign);
+            Ns *= R;
+        }
+    }
+}
+
+constexpr int COL_THREADS = 256;
+constexpr int COL_EPT = 8;
+constexpr int PLANE_THREADS = 512;
+constexpr int PLANE_EPT = 8;
+
+// ------------------------------------------------------------------ kernels
+template <typename T2>
+__global__ void __launch_bounds__(COL_THREADS)
+col_inverse_kernel(const T2* __restrict__ psi, const int* __restrict__ rowmap, long ldpsi, T2* __restrict__ colbuf,
+                   const int* __restrict__ col_start, const int* __restrict__ ent_col, const int* __restrict__ ent_z,
+                   int ncol, int cpb, FftPlan<T2> pz) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* lines = reinterpret_cast<T2*>(smem_raw);
+    const int n2 = pz.n;
+    const int band = blockIdx.y;
+    const int c0 = blockIdx.x * cpb;
+    const int nc = min(cpb, ncol - c0);
+    const long src = rowmap ? rowmap[band] : band;
+    for (int i = threadIdx.x; i < nc * n2; i += blockDim.x) lines[i] = mk((typename real_of<T2>::t)0, (typename real_of<T2>::t)0);
+    __syncthreads();
+    const int g0 = col_start[c0], g1 = col_start[c0 + nc];
+    const T2* p = psi + src * ldpsi;
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) lines[(ent_col[g] - c0) * n2 + ent_z[g]] = p[g];
+    __syncthreads();
+    fft_lines<T2, COL_EPT>(lines, pz, nc, n2, 1, +1);
+    T2* out = colbuf + (long)band * n2 * ncol;
+    for (int i = threadIdx.x; i < nc * n2; i += blockDim.x) {
+        int z = i / nc, cc = i - z * nc;
+        out[(long)z * ncol + c0 + cc] = lines[cc * n2 + z];
+    }
+}
+
+template <typename T2, typename R>
+__global__ void __launch_bounds__(PLANE_THREADS)
+plane_kernel(T2* __restrict__ colbuf, const int* __restrict__ col_xy, int ncol, const R* __restrict__ vz,
+             FftPlan<T2> px, FftPlan<T2> py) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* plane = reinterpret_cast<T2*>(smem_raw);
+    const int n0 = px.n, n1 = py.n, n2 = gridDim.x;
+    const int z = blockIdx.x, band = blockIdx.y;
+    const int np = n0 * n1;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) plane[i] = mk((R)0, (R)0);
+    __syncthreads();
+    T2* cb = colbuf + ((long)band * n2 + z) * ncol;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) plane[col_xy[c]] = cb[c];
+    __syncthreads();
+    fft_lines<T2, PLANE_EPT>(plane, py, n0, n1, 1, +1);   // along y (contiguous rows)
+    fft_lines<T2, PLANE_EPT>(plane, px, n1, 1, n1, +1);   // along x
+    const R* v = vz + (long)z * np;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) plane[i] = cscale(plane[i], v[i]);
+    __syncthreads();
+    fft_lines<T2, PLANE_EPT>(plane, px, n1, 1, n1, -1);
+    fft_lines<T2, PLANE_EPT>(plane, py, n0, n1, 1, -1);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) cb[c] = plane[col_xy[c]];
+}
+
+template <typename T2>
+__global__ void __launch_bounds__(COL_THREADS)
+col_forward_kernel(const T2* __restrict__ colbuf, const T2* __restrict__ psi, const int* __restrict__ rowmap,
+                   long ldpsi, T2* __restrict__ hpsi, const int* __restrict__ col_start,
+                   const int* __restrict__ ent_col, const int* __restrict__ ent_z, const double* __restrict__ kin,
+                   int ncol, int cpb, FftPlan<T2> pz, double inv_ng, double shift, long npw) {
+    using R = typename real_of<T2>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* lines = reinterpret_cast<T2*>(smem_raw);
+    const int n2 = pz.n;
+    const int band = blockIdx.y;
+    const int c0 = blockIdx.x * cpb;
+    const int nc = min(cpb, ncol - c0);
+    const T2* in = colbuf + (long)band * n2 * ncol;
+    for (int i = threadIdx.x; i < nc * n2; i += blockDim.x) {
+        int z = i / nc, cc = i - z * nc;
+        lines[cc * n2 + z] = in[(long)z * ncol + c0 + cc];
+    }
+    __syncthreads();
+    fft_lines<T2, COL_EPT>(lines, pz, nc, n2, 1, -1);
+    const int g0 = col_start[c0], g1 = col_start[c0 + nc];
+    const long src = rowmap ? rowmap[band] : band;
+    const T2* p = psi + src * ldpsi;
+    T2* o = hpsi + (long)band * npw;
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        T2 a = lines[(ent_col[g] - c0) * n2 + ent_z[g]];
+        T2 x = p[g];
+        R f = (R)(kin[g] - shift);
+        o[g] = mk((R)(a.x * (R)inv_ng) + f * x.x, (R)(a.y * (R)inv_ng) + f * x.y);
+    }
+}
+
+// Q[b][a*np + i] = sum_j D[a][i][j] P[b][a*np + j]
+template <typename T2>
+__global__ void apply_D_kernel(const T2* __restrict__ P, T2* __restrict__ Q, const double* __restrict__ D, int natom,
+                               int nproj, int nb) {
+    using R = typename real_of<T2>::t;
+    long total = (long)nb * natom * nproj;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        int i = (int)(t % nproj);
+        long ba = t / nproj;
+        int a = (int)(ba % natom);
+        const T2* pr = P + ba * nproj;
+        const double* d = D + ((long)a * nproj + i) * nproj;
+        double sx = 0, sy = 0;
+        for (int j = 0; j < nproj; ++j) {
+            sx += d[j] * (double)pr[j].x;
+            sy += d[j] * (double)pr[j].y;
+        }
+        Q[t] = mk((R)sx, (R)sy);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static int col_smem(int cpb, int n2, size_t esz) { return (int)(cpb * n2 * esz); }
+
+template <typename T2> static const FftPlan<T2>& plan_of(fs_ctx* c, int d);
+template <> const FftPlan<double2>& plan_of<double2>(fs_ctx* c, int d) { return c->plan64[d]; }
+template <> const FftPlan<float2>& plan_of<float2>(fs_ctx* c, int d) { return c->plan32[d]; }
+
+static std::vector<int> factor_radices(int n) {
+    std::vector<int> r;
+    while (n % 4 == 0) { r.push_back(4); n /= 4; }
+    while (n % 2 == 0) { r.push_back(2); n /= 2; }
+    while (n % 3 == 0) { r.push_back(3); n /= 3; }
+    while (n % 5 == 0) { r.push_back(5); n /= 5; }
+    if (n != 1) return {};
+    return r;
+}
+
+// lines of length n that one block of `threads` threads with element budget ept can hold
+static int group_lines(int n, const std::vector<int>& rads, int threads, int ept) {
+    int cap = 1 << 30;
+    for (int R : rads) {
+        int km = (ept + R - 1) / R;
+        cap = std::min(cap, threads * km * R);
+    }
+    return cap / n;
+}
+
+template <typename T2> static void set_attr_smem(const void* fn, int bytes) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+void ctx_prepare_fft(fs_ctx* c) {
+    for (int d = 0; d < 3; ++d) {
+        int n = c->n[d];
+        std::vector<int> rads = factor_radices(n);
+        if (rads.empty() || (int)rads.size() > FS_MAX_STAGES)
+            throw fs_error(FS_ERR_ARG, "grid size " + std::to_string(n) + " is not of the form 2^a 3^b 5^c");
+        std::vector<double2> t64(n);
+        std::vector<float2> t32(n);
+        for (int p = 0; p < n; ++p) {
+            // exp(-2 pi i p / n), from the exact rational angle
+            double ang = -2.0 * M_PI * (double)p / (double)n;
+            t64[p] = make_double2(std::cos(ang), std::sin(ang));
+            t32[p] = make_float2((float)t64[p].x, (float)t64[p].y);
+        }
+        c->tw64[d].alloc(n * sizeof(double2));
+        c->tw32[d].alloc(n * sizeof(float2));
+        FS_CUDA(cudaMemcpy(c->tw64[d].p, t64.data(), n * sizeof(double2), cudaMemcpyHostToDevice));
+        FS_CUDA(cudaMemcpy(c->tw32[d].p, t32.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+        int threads = (d == 2) ? COL_THREADS : PLANE_THREADS;
+        int ept = (d == 2) ? COL_EPT : PLANE_EPT;
+        int grp = group_lines(n, rads, threads, ept);
+        if (grp < 1) throw fs_error(FS_ERR_ARG, "FFT length " + std::to_string(n) + " too long for one block");
+        FftPlan<double2> p64{};
+        FftPlan<float2> p32{};
+        p64.n = p32.n = n;
+        p64.nst = p32.nst = (int)rads.size();
+        for (size_t s = 0; s < rads.size(); ++s) p64.rad[s] = p32.rad[s] = rads[s];
+        p64.group = p32.group = grp;
+        p64.tw = c->tw64[d].as<double2>();
+        p32.tw = c->tw32[d].as<float2>();
+        c->plan64[d] = p64;
+        c->plan32[d] = p32;
+    }
+    size_t plane64 = (size_t)c->n[0] * c->n[1] * sizeof(double2);
+    if (plane64 > 227 * 1024)
+        throw fs_error(FS_ERR_ARG, "n0 * n1 plane does not fit in shared memory");
+    c->cpb = 16;
+    while (c->cpb > 1 && (size_t)col_smem(c->cpb, c->n[2], sizeof(double2)) > 200 * 1024) c->cpb /= 2;
+    set_attr_smem<double2>((const void*)col_inverse_kernel<double2>, col_smem(c->cpb, c->n[2], sizeof(double2)));
+    set_attr_smem<double2>((const void*)col_forward_kernel<double2>, col_smem(c->cpb, c->n[2], sizeof(double2)));
+    set_attr_smem<float2>((const void*)col_inverse_kernel<float2>, col_smem(c->cpb, c->n[2], sizeof(float2)));
+    set_attr_smem<float2>((const void*)col_forward_kernel<float2>, col_smem(c->cpb, c->n[2], sizeof(float2)));
+    set_attr_smem<double2>((const void*)plane_kernel<double2, double>, (int)plane64);
+    set_attr_smem<float2>((const void*)plane_kernel<float2, float>, (int)(plane64 / 2));
+}
+
+template <typename T2> static const void* vz_of(fs_ctx* c);
+template <> const void* vz_of<double2>(fs_ctx* c) { return c->vz64.p; }
+template <> const void* vz_of<float2>(fs_ctx* c) { return c->vz32.p; }
+template <typename T2> static const T2* beta_of(fs_ctx* c);
+template <> const double2* beta_of<double2>(fs_ctx* c) { return c->beta64.as<double2>(); }
+template <> const float2* beta_of<float2>(fs_ctx* c) { return c->beta32.as<float2>(); }
+
+// Bands are processed in chunks so that the column buffer stays bounded.
+template <typename T2>
+void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, const int* rowmap) {
+    using R = typename real_of<T2>::t;
+    if (nb <= 0) return;
+    const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    const long colband = (long)n2 * c->ncol;
+    const long max_chunk_bytes = 2L << 30;  // 2 GiB of column buffer
+    int chunk = (int)std::max(1L, std::min((long)nb, max_chunk_bytes / (colband * (long)sizeof(T2))));
+    c->colbuf.ensure((size_t)chunk * colband * sizeof(T2));
+    T2* cb = c->colbuf.as<T2>();
+    const FftPlan<T2>& px = plan_of<T2>(c, 0);
+    const FftPlan<T2>& py = plan_of<T2>(c, 1);
+    const FftPlan<T2>& pz = plan_of<T2>(c, 2);
+    const int cpb = c->cpb;
+    const int ncb = (c->ncol + cpb - 1) / cpb;
+    const int csm = col_smem(cpb, n2, sizeof(T2));
+    const int psm = n0 * n1 * (int)sizeof(T2);
+    const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
+    for (int b0 = 0; b0 < nb; b0 += chunk) {
+        int nbc = std::min(chunk, nb - b0);
+        const T2* src = rowmap ? psi : psi + (long)b0 * c->npw;
+        const int* rm = rowmap ? rowmap + b0 : nullptr;
+        dim3 gc(ncb, nbc);
+        col_inverse_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(src, rm, c->npw, cb, c->col_start.as<int>(),
+                                                                     c->ent_col.as<int>(), c->ent_z.as<int>(),
+                                                                     c->ncol, cpb, pz);
+        dim3 gp(n2, nbc);
+        plane_kernel<T2, R><<<gp, PLANE_THREADS, psm, c->stream>>>(cb, c->col_xy.as<int>(), c->ncol,
+                                                                   (const R*)vz_of<T2>(c), px, py);
+        col_forward_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(
+            cb, src, rm, c->npw, hpsi + (long)b0 * c->npw, c->col_start.as<int>(), c->ent_col.as<int>(),
+            c->ent_z.as<int>(), c->kin.as<double>(), c->ncol, cpb, pz, inv_ng, shift, c->npw);
+        FS_CUDA(cudaGetLastError());
+    }
+    if (c->nptot > 0) {
+        // P[b][p] = sum_g conj(beta[p][g]) psi[b][g]   -> written as P[b * nptot + p]
+        c->projbuf.ensure((size_t)nb * c->nptot * sizeof(double2));
+        c->projbuf2.ensure((size_t)nb * c->nptot * sizeof(double2));
+        double2* P = c->projbuf.as<double2>();
+        gemm_gram<T2>(c, c->nptot, nb, c->npw, beta_of<T2>(c), c->npw, nullptr, psi, c->npw, rowmap, P, 1,
+                      c->nptot, 1.0, 0.0);
+        double2* Q = c->projbuf2.as<double2>();
+        int blocks = (int)std::min<long>(4096, ((long)nb * c->nptot + 255) / 256);
+        apply_D_kernel<double2><<<blocks, 256, 0, c->stream>>>(P, Q, c->Dmat.as<double>(), c->natom, c->nproj, nb);
+        FS_CUDA(cudaGetLastError());
+        // hpsi[b][g] += sum_p Q[b][p] beta[p][g]
+        gemm_nn<T2, double2>(c, nb, c->npw, c->nptot, Q, c->nptot, 1, beta_of<T2>(c), c->npw, nullptr, hpsi,
+                             c->npw, nullptr, 1.0, 1.0, hpsi, c->npw);
+    }
+}
+
+template void apply_H_impl<double2>(fs_ctx*, const double2*, double2*, int, double, const int*);
+template void apply_H_impl<float2>(fs_ctx*, const float2*, float2*, int, double, const int*);

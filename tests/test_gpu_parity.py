@@ -1,0 +1,119 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
+
+H application: element by element against the oracle's matrix-free H on the
+same seeded inputs, FP64 to 1e-12 relative, FP32 to 2e-6 relative (a few FP32
+roundings per FFT stage of log2 N stages).  Solve: eigenvalues against LAPACK
+brute force to |d eps| <= 1e-5 Ha, every returned state's residual
+||H psi - eps psi|| recomputed by the oracle <= 1e-6, orthonormality.
+"""
+import numpy as np
+import pytest
+
+import fs_inputs as fi
+from oracle import planewave as pw
+from gpu_helpers import CASES, rel_err, small_box
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_EPS = 1e-5       # Ha
+TOL_RES = 1e-6       # ||H psi - eps psi||
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_1907_06821_gb300 import build as b
+    b.build()
+    import paper_1907_06821_gb300 as m
+    return m
+
+
+def make_ctx(fs, w, **kw):
+    return fs.Context.from_workload(w, **kw)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_sphere_order_matches_oracle(fs, case):
+    w = CASES[case]()
+    with make_ctx(fs, w) as c:
+        g, _ = pw.sphere(w.L, w.n, w.ecut, w.k)
+        assert c.npw == g.shape[0]
+        assert np.array_equal(c.gvectors(), g.astype(np.int32))
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("nband", [1, 13, 70])
+def test_apply_H_fp64(fs, case, nband):
+    w = CASES[case]()
+    h = pw.Hamiltonian(w)
+    X = fi.raw_start_block(nband, h.npw, 100 + nband)
+    ref = h.apply(X, 0.25)
+    with make_ctx(fs, w) as c:
+        psi = torch.from_numpy(X).cuda()
+        out = c.apply_H(psi, shift=0.25).cpu().numpy()
+    assert rel_err(out, ref) < 1e-12
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_apply_H_fp32(fs, case):
+    w = CASES[case]()
+    h = pw.Hamiltonian(w)
+    X = fi.raw_start_block(9, h.npw, 7).astype(np.complex64)
+    ref = h.apply(X.astype(np.complex128), -0.1)
+    with make_ctx(fs, w, precision=fs.FS_MIXED) as c:
+        out = c.apply_H(torch.from_numpy(X).cuda(), shift=-0.1).cpu().numpy()
+    assert rel_err(out.astype(np.complex128), ref) < 2e-6
+
+
+def test_apply_H_is_deterministic(fs):
+    w = CASES["box_radix5_two_widths"]()
+    with make_ctx(fs, w) as c:
+        psi = torch.from_numpy(fi.raw_start_block(17, c.npw, 3)).cuda()
+        a = c.apply_H(psi).cpu().numpy()
+        b = c.apply_H(psi).cpu().numpy()
+    assert np.array_equal(a.view(np.float64), b.view(np.float64))
+
+
+def test_apply_H_empty_and_bad_args(fs):
+    w = CASES["tiny"]()
+    with make_ctx(fs, w) as c:
+        e = torch.empty((0, c.npw), dtype=torch.complex128, device="cuda")
+        assert c.apply_H(e).shape == (0, c.npw)
+        psi = torch.zeros((2, c.npw), dtype=torch.complex128, device="cuda")
+        p = psi.data_ptr()
+        assert c.lib.fs_apply_H(c.h, p, p, 2, 0.0, fs.FS_FP64) == fs.FS_ERR_ARG      # aliasing
+        assert c.lib.fs_apply_H(c.h, p, p + 16, -1, 0.0, fs.FS_FP64) == fs.FS_ERR_ARG  # negative count
+        assert c.lib.fs_apply_H(c.h, p, p + 16, 1, 0.0, 7) == fs.FS_ERR_ARG            # precision
+        assert c.lib.fs_last_error(c.h) != b""
+
+
+def test_grid_too_small_is_reported(fs):
+    w = fi.make_config("tiny")
+    with pytest.raises(fs.FSError) as ei:
+        fs.Context(w.L, w.n, 20.0, w.k, w.vloc, pos=w.pos, proj=w.proj, D=w.D)
+    assert ei.value.code == fs.FS_ERR_GRID_TOO_SMALL
+
+
+def _check_solution(w, r, states, eb):
+    assert np.abs(r["eps"] - eb).max() <= TOL_EPS
+    h = pw.Hamiltonian(w)
+    HX = h.apply(states)
+    res = np.linalg.norm(HX - r["eps"][:, None] * states, axis=1)
+    assert res.max() <= TOL_RES
+    assert np.allclose(res, r["resid"], atol=1e-8)
+    S = states.conj() @ states.T
+    assert np.abs(S - np.eye(states.shape[0])).max() < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["tiny", "box_radix5_two_widths", "box_k_radix35"])
+def test_solve_matches_lapack(fs, case, precision):
+    w = CASES[case]()
+    eb, _, _ = pw.brute_nearest(w, w.e_ref, w.nstates)
+    prec = fs.FS_FP64 if precision == "fp64" else fs.FS_MIXED
+    with make_ctx(fs, w, precision=prec) as c:
+        c.set_initial_states(fi.raw_start_block(w.nbands, c.npw, 17), damp=True)
+        r = c.solve(w.e_ref, w.nstates, tol=TOL_RES)
+        states = c.get_states(w.nstates)
+    assert r["nconv"] == w.nstates
+    _check_solution(w, r, states, eb)
