@@ -1,0 +1,311 @@
+"""Benchmark of the folded-spectrum eigensolve (one JSON line on rank 0).
+
+A step is one complete solve, from the same seeded start block, of the
+wire-segment workload: 40x40x80 bohr cell, 72x72x144 grid, 20 Ry cutoff
+(193,673 plane waves), 256 Gaussian wells, 8 projectors per atom, the 256
+states nearest the reference energy, to residual 1e-6.  The metric is states
+converged per second (residual <= 1e-6 by the library's FP64 check).
+
+  python bench.py [--steps K] [--warmup W] [--precision mixed|fp64]
+                  [--workload wire|tiny] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (test infrastructure, the only
+other code path here) on a bounded sample of the same workload.  Under
+torchrun each rank solves its own seeded instance (independent problems, no
+collective on the data path; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "states converged/s to 1e-6 residual (mixed+learned vs plain FP64); Hψ HBM GB/s"
+TOL = 1e-6
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name, rank):
+    import fs_inputs as fi
+    if name == "wire":
+        return fi.make_config("wire", seed=1908 + 1000 * rank) if rank else fi.make_config("wire")
+    return fi.make_config(name)
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    res = cpu_baseline(args.workload, None)
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": "states/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["seconds_per_solve"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {res['desc']}", "sample": res["sample"]},
+            "cpu_baseline": {"value": res["value"], "unit": "states/s", "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(name, gpu_counts):
+    """Time the CPU FP64 oracle on a bounded sample of the workload and scale
+    it to one solve with the GPU solve's operation counts (or, without them,
+    with the iteration count the oracle needs on the tiny workload)."""
+    import fs_inputs as fi
+    from oracle import planewave as pw
+    w = workload(name, 0)
+    cores = os.cpu_count()
+    t0 = time.time()
+    h = pw.Hamiltonian(w)
+    t_setup = time.time() - t0
+    nb = 8
+    X = fi.raw_start_block(nb, h.npw, 3)
+    t0 = time.time()
+    h.apply(X, w.e_ref)
+    t_h = (time.time() - t0) / nb                      # seconds per band application of H
+    m = w.nbands
+    Xb = fi.raw_start_block(m, h.npw, 4)
+    t0 = time.time()
+    _ = Xb.conj() @ Xb.T
+    t_gram = time.time() - t0                            # one m x m Gram product, K = npw
+    gram_flops = 8.0 * m * m * h.npw
+    if gpu_counts is None:
+        # per iteration: 2 m band applications of H + about 9 m x m-sized Gram-type products
+        per_iter = 2 * m * t_h + 9 * 4 * t_gram
+        iters = gpu_counts_iters = 150
+        est = iters * per_iter
+        how = f"assumed {gpu_counts_iters} iterations"
+    else:
+        est = gpu_counts["n_hpsi"] * t_h + gpu_counts["gemm_flops"] / gram_flops * t_gram
+        how = "scaled by the GPU solve's H applications and GEMM flops"
+    value = w.nstates / est
+    sample = (f"oracle H on {nb} bands ({t_h * 1e3:.1f} ms/band) and one {m}x{m} Gram product over "
+              f"{h.npw} plane waves ({t_gram:.2f} s), {how}; setup {t_setup:.1f} s")
+    return dict(value=value, cores=cores, sample=sample, seconds_per_solve=est,
+                desc=f"grid {w.n}, {h.npw} PWs, {w.natom} atoms, {w.nproj} proj/atom, {w.nstates} states")
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import fs_inputs as fi
+    import paper_1907_06821_gb300 as fs
+    from paper_1907_06821_gb300 import build as b
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    b.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workload(args.workload, rank)
+    prec = fs.FS_MIXED if args.precision == "mixed" else fs.FS_FP64
+    stream = torch.cuda.Stream(device=dev)
+    ctx = fs.Context.from_workload(w, precision=prec, maxit=args.maxit, stream=stream.cuda_stream,
+                                   seed=1907)
+    x0_host = fi.raw_start_block(w.nbands, ctx.npw, 17)
+    x0_dev = torch.from_numpy(x0_host).to(dev)
+    torch.cuda.synchronize()
+
+    def step():
+        ctx.set_initial_states(x0_dev, damp=True)
+        return ctx.solve(w.e_ref, w.nstates, tol=TOL, allow_unconverged=True)
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler(dev.index if ws == 1 else local)
+    ctx.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_dev = ev0.elapsed_time(ev1) / 1e3
+    stats = ctx.kernel_stats()
+    ctx.profile(False)
+    # end-to-end through the C ABI with host buffers: start block H2D, solve, states D2H
+    t0 = time.time()
+    e2e_states = 0
+    for _ in range(args.steps):
+        ctx.set_initial_states(x0_host, damp=True)
+        r = ctx.solve(w.e_ref, w.nstates, tol=TOL, allow_unconverged=True)
+        _ = ctx.get_states(w.nstates)
+        e2e_states += r["nconv"]
+    t_e2e = time.time() - t0
+    nconv = sum(r["nconv"] for r in results)
+    tmax = t_dev
+    if dist:
+        tt = torch.tensor([t_dev, float(nconv), t_e2e, float(e2e_states)], device=dev)
+        gathered = [torch.zeros_like(tt) for _ in range(ws)]
+        dist.all_gather(gathered, tt)
+        tmax = max(float(g[0]) for g in gathered)
+        nconv = sum(int(g[1]) for g in gathered)
+        t_e2e = max(float(g[2]) for g in gathered)
+        e2e_states = sum(int(g[3]) for g in gathered)
+    if rank == 0:
+        hbm, bf16, smax, src = peaks()
+        line = make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, clocks, hbm, src, ws,
+                         x0_host)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, clocks, hbm, src, ws, x0_host):
+    r0 = results[0]
+    hpsi = ("col_inverse_fft", "plane_fft_vloc", "col_forward_fft")
+    hpsi_ms = sum(stats[k]["ms"] for k in hpsi)
+    hpsi_bytes = sum(stats[k]["bytes"] for k in hpsi)
+    top = max(stats, key=lambda k: stats[k]["ms"])
+    fp32 = args.precision == "mixed"
+    alu_peak = 152 * 128 * 2 * 2.07e9 / 1e12 / (1 if fp32 else 64)     # FP32 (or FP64) CUDA-core TFLOP/s
+    st = stats[top]
+    if top in ("gram", "rotate", "nonlocal_project", "nonlocal_add", "dense_la"):
+        achieved = st["flops"] / (st["ms"] / 1e3) / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": "FP32 CUDA-core peak 152 SMs x 128 lanes x 2 x 2.07 GHz" if fp32 else
+                "FP64 CUDA-core peak (1/64 of FP32)"}
+    else:
+        achieved = st["bytes"] / (st["ms"] / 1e3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": f"{src} hbm_gbs"}
+    gemm_flops = sum(stats[k]["flops"] for k in ("gram", "rotate", "nonlocal_project", "nonlocal_add"))
+    n_hpsi = sum(r["n_hpsi"] for r in results) / len(results)
+    counts = {"n_hpsi": n_hpsi, "gemm_flops": gemm_flops / len(results)}
+    cpu = None
+    if not args.no_cpu and ws == 1:
+        c = cpu_baseline(args.workload, counts)
+        cpu = {"value": c["value"], "unit": "states/s", "cores": c["cores"], "kind": "oracle", "sample": c["sample"]}
+    total_ms = sum(v["ms"] for v in stats.values())
+    return {
+        "metric": METRIC, "value": nconv / tmax, "unit": "states/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: grid {tuple(w.n)}, {ctx.npw} PWs, {w.natom} atoms, "
+                               f"{w.nproj} proj/atom, {w.nstates} states nearest E_ref={w.e_ref:.6f} Ha",
+                   "precision": args.precision, "tol": TOL, "l2": "inputs larger than L2 (each band block "
+                   f"{w.nbands * ctx.npw * (8 if fp32 else 16) / 1e6:.0f} MB)", "start_block_seed": 17},
+        "roofline": roof,
+        "hpsi_gbs": hpsi_bytes / (hpsi_ms / 1e3) / 1e9 if hpsi_ms > 0 else None,
+        "hpsi_frac_hbm": (hpsi_bytes / (hpsi_ms / 1e3) / 1e9) / hbm if hpsi_ms > 0 else None,
+        "kernel_time_share": {k: round(v["ms"] / total_ms, 4) for k, v in stats.items() if total_ms > 0},
+        "solve": {"nconv": r0["nconv"], "iters": r0["iters"], "iters_mixed": r0["iters_mixed"],
+                  "n_hpsi": r0["n_hpsi"], "max_resid": float(np.max(r0["resid"])), "status": r0["status"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_states / t_e2e, "unit": "states/s",
+                "h2d_bytes_per_step": int(x0_host.nbytes), "d2h_bytes_per_step": int(w.nstates * ctx.npw * 16)},
+        "gpu_launches": int(sum(v["launches"] for v in stats.values())),
+        "clocks": clocks,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="wire", choices=["wire", "tiny"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--maxit", type=int, default=3000)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

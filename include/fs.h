@@ -60,6 +60,7 @@ typedef enum {
 enum { FS_FP64 = 0, FS_MIXED = 1 };                     /* arithmetic of the vector work */
 enum { FS_PREC_M = 0, FS_PREC_TETER = 1, FS_PREC_LEARNED = 2 };
 enum { FS_HOST = 0, FS_DEVICE = 1 };                     /* where a state buffer lives */
+enum { FS_GEMM_TENSOR = 0, FS_GEMM_CUDA_CORES = 1 };     /* FP32-stage GEMM engine */
 
 /* Orthorhombic cell (bohr) and FFT grid.  Grid point j sits at r_j = (j_d L_d / n_d). */
 typedef struct {
@@ -93,6 +94,8 @@ typedef struct {
     unsigned long long seed;   /* start block when none is supplied */
     void* cuda_stream;         /* cudaStream_t to run on (NULL: the library's own stream) */
     int verbose;               /* > 0: one line per iteration on stderr */
+    int gemm_path;             /* FP32-stage GEMMs: FS_GEMM_TENSOR (default, tcgen05 TF32 x3 split)
+                                  or FS_GEMM_CUDA_CORES (FP32 FMA); FP64 work always uses FP64 FMA */
 } fs_options;
 
 typedef struct {
@@ -141,6 +144,25 @@ fs_status fs_solve(fs_ctx* ctx, double e_ref, int nstates, double tol, fs_result
 /* Copy the n first states of the last solve (in the order of res->eps),
  * [n][npw] complex128, to host or device memory. */
 fs_status fs_get_states(fs_ctx* ctx, void* psi, int n, int where);
+
+/* Per-kernel-class timing.  fs_profile(ctx, 1) resets the counters and
+ * starts recording a CUDA event pair on the context's stream around every
+ * launch of the library's kernels (and around its small dense FP64 solves);
+ * fs_profile(ctx, 0) stops.  fs_kernel_stats copies up to max entries: the
+ * class name (static string), launches, summed event time (ms), and the
+ * algorithmic bytes and flops of those launches (the minimum traffic the
+ * kernel's function implies: each operand read once, each result written
+ * once).  *count receives the number of classes. */
+typedef struct {
+    const char* name;
+    long long launches;
+    double ms;
+    double bytes;
+    double flops;
+} fs_kernel_stat;
+
+fs_status fs_profile(fs_ctx* ctx, int enable);
+fs_status fs_kernel_stats(fs_ctx* ctx, fs_kernel_stat* out, int max, int* count);
 
 /* Release everything the context holds.  NULL is accepted. */
 void fs_destroy(fs_ctx* ctx);

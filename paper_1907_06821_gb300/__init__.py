@@ -21,6 +21,7 @@ FS_OK, FS_ERR_ARG, FS_ERR_GRID_TOO_SMALL, FS_ERR_OOM, FS_ERR_CUDA, FS_ERR_NUMERI
 FS_FP64, FS_MIXED = 0, 1
 FS_PREC_M, FS_PREC_TETER, FS_PREC_LEARNED = 0, 1, 2
 FS_HOST, FS_DEVICE = 0, 1
+FS_GEMM_TENSOR, FS_GEMM_CUDA_CORES = 0, 1
 
 STATUS_NAMES = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_GRID_TOO_SMALL", 3: "FS_ERR_OOM",
                 4: "FS_ERR_CUDA", 5: "FS_ERR_NUMERIC", 6: "FS_ERR_NOT_CONVERGED",
@@ -40,13 +41,18 @@ class fs_projectors(C.Structure):
 class fs_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("dE", C.c_double),
                 ("maxit", C.c_int), ("guard", C.c_int), ("seed", C.c_ulonglong),
-                ("cuda_stream", C.c_void_p), ("verbose", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("gemm_path", C.c_int)]
 
 
 class fs_result(C.Structure):
     _fields_ = [("nconv", C.c_int), ("iters", C.c_int), ("n_hpsi", C.c_longlong),
                 ("eps", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
                 ("seconds", C.c_double), ("iters_mixed", C.c_int)]
+
+
+class fs_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double),
+                ("bytes", C.c_double), ("flops", C.c_double)]
 
 
 class FSError(RuntimeError):
@@ -82,6 +88,10 @@ def load_library(path: str = LIB_PATH):
     lib.fs_solve.restype = ip
     lib.fs_get_states.argtypes = [vp, vp, ip, ip]
     lib.fs_get_states.restype = ip
+    lib.fs_profile.argtypes = [vp, ip]
+    lib.fs_profile.restype = ip
+    lib.fs_kernel_stats.argtypes = [vp, C.POINTER(fs_kernel_stat), ip, C.POINTER(C.c_int)]
+    lib.fs_kernel_stats.restype = ip
     lib.fs_destroy.argtypes = [vp]
     lib.fs_destroy.restype = None
     lib.fs_last_error.argtypes = [vp]
@@ -107,7 +117,8 @@ class Context:
     """
 
     def __init__(self, L, n, ecut, k, vloc, pos=None, proj=(), D=None, precision=FS_FP64,
-                 precond=FS_PREC_M, dE=0.5, maxit=5000, guard=-1, seed=1, stream=None, verbose=0):
+                 precond=FS_PREC_M, dE=0.5, maxit=5000, guard=-1, seed=1, stream=None, verbose=0,
+                 gemm_path=FS_GEMM_TENSOR):
         self.lib = load_library()
         self._keep = []
         g = fs_grid((C.c_double * 3)(*[float(x) for x in L]), (C.c_int * 3)(*[int(x) for x in n]))
@@ -127,7 +138,7 @@ class Context:
             pr.natom, pr.nproj = posa.shape[0], len(proj)
             pr.pos, pr.l, pr.axis, pr.width, pr.D = _dptr(posa), _iptr(la), _iptr(axa), _dptr(wa), _dptr(Da)
         opt = fs_options(precision, precond, dE, maxit, guard, seed,
-                         C.c_void_p(stream) if stream else None, verbose)
+                         C.c_void_p(stream) if stream else None, verbose, gemm_path)
         self.precision = precision
         h = C.c_void_p()
         st = self.lib.fs_create(C.byref(g), float(ecut), _dptr(kk), _dptr(v), C.byref(pr), C.byref(opt),
@@ -204,6 +215,18 @@ class Context:
         self._check(self.lib.fs_get_states(self.h, out.ctypes.data_as(C.c_void_p), n, FS_HOST),
                     "fs_get_states")
         return out
+
+    def profile(self, enable=True):
+        """Reset and start (or stop) per-kernel-class event timing."""
+        self._check(self.lib.fs_profile(self.h, int(enable)), "fs_profile")
+
+    def kernel_stats(self):
+        """{class: dict(launches, ms, bytes, flops)} since the last profile(True)."""
+        arr = (fs_kernel_stat * 32)()
+        n = C.c_int()
+        self._check(self.lib.fs_kernel_stats(self.h, arr, 32, C.byref(n)), "fs_kernel_stats")
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes,
+                                           flops=arr[i].flops) for i in range(n.value)}
 
     def close(self):
         if getattr(self, "h", None):

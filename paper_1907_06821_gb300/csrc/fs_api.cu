@@ -186,6 +186,19 @@ void ensure_fp32_tables(fs_ctx* c) {
 
 void ctx_ensure_fp32(fs_ctx* c) { ensure_fp32_tables(c); }
 
+int* ctx_errflag(fs_ctx* c) { return c->errflag.as<int>(); }
+
+// raise FS_ERR_TIMEOUT if a device-side bounded wait gave up (clears the flag)
+void ctx_check_errflag(fs_ctx* c) {
+    int v = 0;
+    FS_CUDA(cudaMemcpyAsync(&v, c->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    if (v) {
+        FS_CUDA(cudaMemsetAsync(c->errflag.p, 0, sizeof(int), c->stream));
+        throw fs_error(FS_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its limit");
+    }
+}
+
 extern "C" {
 
 fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const double* vloc,
@@ -210,6 +223,11 @@ fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const d
         if (c->opt.maxit <= 0) c->opt.maxit = 5000;
         if (c->opt.precision != FS_FP64 && c->opt.precision != FS_MIXED) throw fs_error(FS_ERR_ARG, "bad precision");
         if (c->opt.precond < FS_PREC_M || c->opt.precond > FS_PREC_LEARNED) throw fs_error(FS_ERR_ARG, "bad precond");
+        if (c->opt.gemm_path != FS_GEMM_TENSOR && c->opt.gemm_path != FS_GEMM_CUDA_CORES)
+            throw fs_error(FS_ERR_ARG, "bad gemm_path");
+        c->gemm_path = c->opt.gemm_path;
+        c->errflag.alloc(sizeof(int));
+        FS_CUDA(cudaMemset(c->errflag.p, 0, sizeof(int)));
         if (c->opt.cuda_stream) {
             c->stream = (cudaStream_t)c->opt.cuda_stream;
         } else {
@@ -218,6 +236,8 @@ fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const d
         }
         FS_SOLVER(cusolverDnCreate(&c->solver));
         FS_SOLVER(cusolverDnSetStream(c->solver, c->stream));
+        FS_BLAS(cublasCreate(&c->blas));
+        FS_BLAS(cublasSetStream(c->blas, c->stream));
         build_sphere(c);
         ctx_prepare_fft(c);
         upload_potential(c, vloc);
@@ -247,7 +267,7 @@ fs_status fs_gvectors(const fs_ctx* c, int* miller) {
 
 fs_status fs_apply_H(fs_ctx* c, const void* psi, void* hpsi, int nband, double shift, int precision) {
     if (!c) return FS_ERR_ARG;
-    if (nband < 0 || (nband > 0 && (!psi || !hpsi)) || psi == hpsi || !std::isfinite(shift)) {
+    if (nband < 0 || (nband > 0 && (!psi || !hpsi || psi == hpsi)) || !std::isfinite(shift)) {
         c->err = "fs_apply_H: bad arguments";
         return FS_ERR_ARG;
     }
@@ -264,6 +284,7 @@ fs_status fs_apply_H(fs_ctx* c, const void* psi, void* hpsi, int nband, double s
             apply_H_impl<float2>(c, (const float2*)psi, (float2*)hpsi, nband, shift);
         }
         FS_CUDA(cudaStreamSynchronize(c->stream));
+        ctx_check_errflag(c);
     });
 }
 
@@ -314,7 +335,9 @@ fs_status fs_get_states(fs_ctx* c, void* psi, int n, int where) {
 void fs_destroy(fs_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    prof_release(c);
     if (c->solver) cusolverDnDestroy(c->solver);
+    if (c->blas) cublasDestroy(c->blas);
     cudaStream_t s = c->stream;
     bool own = c->own_stream;
     delete c;

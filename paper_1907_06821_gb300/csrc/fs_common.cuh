@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cublas_v2.h>
 #include <cusolverDn.h>
 
 #include <cstdint>
@@ -63,6 +64,14 @@ template <typename T2> struct FftPlan {
         }                                                                                \
     } while (0)
 
+#define FS_BLAS(call)                                                                    \
+    do {                                                                                 \
+        cublasStatus_t s_ = (call);                                                      \
+        if (s_ != CUBLAS_STATUS_SUCCESS) {                                               \
+            throw fs_error(FS_ERR_CUDA, std::string(#call) + ": cublas status " + std::to_string((int)s_)); \
+        }                                                                                \
+    } while (0)
+
 #define FS_SOLVER(call)                                                                  \
     do {                                                                                 \
         cusolverStatus_t s_ = (call);                                                    \
@@ -107,6 +116,37 @@ struct dbuf {
     dbuf& operator=(const dbuf&) = delete;
 };
 
+// ------------------------------------------------------------------ kernel timing
+// Optional per-kernel-class timing with CUDA events on the context's stream
+// (enabled by fs_profile); each launch also adds its algorithmic bytes/flops.
+enum {
+    KS_COL_INV = 0,  // unpack + inverse z-FFT
+    KS_PLANE,        // xy-plane FFTs with the V(r) multiply
+    KS_COL_FWD,      // forward z-FFT + pack + kinetic/shift
+    KS_NL_PROJ,      // <beta|psi> projections
+    KS_NL_D,         // D contraction per atom
+    KS_NL_ADD,       // hpsi += beta Q
+    KS_GRAM,         // solver Gram matrices / inner products
+    KS_ROTATE,       // solver basis rotations and projections
+    KS_VECTOR,       // residuals, preconditioner, norms, scaling
+    KS_DENSE_LA,     // FP64 small dense eigensolves and products
+    KS_COUNT
+};
+struct KStat {
+    long long launches = 0;
+    double ms = 0, bytes = 0, flops = 0;
+};
+struct Prof {
+    bool on = false;
+    KStat st[KS_COUNT];
+    struct Pend {
+        int id;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pend> pend;
+    std::vector<cudaEvent_t> pool;
+};
+
 // ------------------------------------------------------------------ context
 struct fs_ctx {
     // geometry and basis
@@ -124,6 +164,7 @@ struct fs_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cusolverDnHandle_t solver = nullptr;
+    cublasHandle_t blas = nullptr;
 
     // basis tables (device)
     dbuf col_start;   // int [ncol+1]
@@ -157,7 +198,21 @@ struct fs_ctx {
     dbuf result_states;  // double2 [nstates][npw]
     int nresult = 0;
 
+    Prof prof;
+    dbuf errflag;     // int: set by a device-side wait that gave up
+    int gemm_path = 0;
     std::string err;
+};
+
+void prof_flush(fs_ctx* c);
+void prof_release(fs_ctx* c);
+// RAII scope around one launch (or a short sequence) of kernel class id
+struct ProfScope {
+    fs_ctx* c;
+    int id;
+    cudaEvent_t a = nullptr;
+    ProfScope(fs_ctx* c_, int id_, double bytes, double flops);
+    ~ProfScope();
 };
 
 // ------------------------------------------------------------------ internal entry points
@@ -173,12 +228,22 @@ void ctx_prepare_fft(fs_ctx* c);
 // C(i, j) is written as double2 at C[i * ci + j * cj].
 template <typename T2>
 void gemm_gram(fs_ctx* c, int M, int N, int K, const T2* A, long lda, const int* amap, const T2* B, long ldb,
-               const int* bmap, double2* C, long ci, long cj, double alpha, double beta);
+               const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid = KS_GRAM);
 // Rotation/apply form: C[ic(i)][n] = alpha * sum_k Acoef(i, k) * B[ib(k)][n] + beta * D[ic(i)][n]
 // Acoef(i, k) = A[i * ai + k * ak] (A2 complex coefficients, double2 or T2);  D may equal C or be null.
 template <typename T2, typename A2>
 void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const T2* B, long ldb, const int* bmap,
-             T2* C, long ldc, const int* cmap, double alpha, double beta, const T2* D, long ldd);
+             T2* C, long ldc, const int* cmap, double alpha, double beta, const T2* D, long ldd, int kid = KS_ROTATE);
+
+// tensor-core GEMMs for the FP32 stage (fs_tc.cu)
+void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, const int* amap, const float2* B,
+                  long ldb, const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid);
+template <typename A2>
+void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const float2* B, long ldb,
+                const int* bmap, float2* C, long ldc, const int* cmap, double alpha, double beta, const float2* D,
+                long ldd, int kid);
+int* ctx_errflag(fs_ctx* c);
+void ctx_check_errflag(fs_ctx* c);
 
 // vector kernels (fs_vec.cu)
 template <typename T2> void vec_resid(fs_ctx* c, const T2* X, const T2* Y, int m, double* resid, double2* dot);

@@ -186,8 +186,15 @@ nn_kernel(int M, int N, int K, const A2* __restrict__ A, long ai_, long ak_, con
 
 template <typename T2>
 void gemm_gram(fs_ctx* c, int M, int N, int K, const T2* A, long lda, const int* amap, const T2* B, long ldb,
-               const int* bmap, double2* C, long ci, long cj, double alpha, double beta) {
+               const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid) {
     if (M <= 0 || N <= 0) return;
+    if constexpr (sizeof(T2) == 8) {
+        if (c->gemm_path == FS_GEMM_TENSOR) {
+            tc_gemm_gram(c, M, N, K, A, lda, amap, B, ldb, bmap, C, ci, cj, alpha, beta, kid);
+            return;
+        }
+    }
+    ProfScope ps(c, kid, ((double)M + N) * K * sizeof(T2) + (double)M * N * sizeof(double2), 8.0 * M * N * K);
     int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
     int want = std::max(1, (2 * 152 + tm * tn - 1) / (tm * tn));
     int maxs = std::max(1, K / 512);
@@ -206,8 +213,16 @@ void gemm_gram(fs_ctx* c, int M, int N, int K, const T2* A, long lda, const int*
 
 template <typename T2, typename A2>
 void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const T2* B, long ldb, const int* bmap,
-             T2* C, long ldc, const int* cmap, double alpha, double beta, const T2* D, long ldd) {
+             T2* C, long ldc, const int* cmap, double alpha, double beta, const T2* D, long ldd, int kid) {
     if (M <= 0 || N <= 0) return;
+    if constexpr (sizeof(T2) == 8) {
+        if (c->gemm_path == FS_GEMM_TENSOR) {
+            tc_gemm_nn<A2>(c, M, N, K, A, ai, ak, B, ldb, bmap, C, ldc, cmap, alpha, beta, D, ldd, kid);
+            return;
+        }
+    }
+    ProfScope ps(c, kid, ((double)K + M * (beta != 0.0 ? 2.0 : 1.0)) * N * sizeof(T2) + (double)M * K * sizeof(A2),
+                 8.0 * M * N * K);
     dim3 g((N + BN - 1) / BN, (M + BM - 1) / BM);
     nn_kernel<T2, A2><<<g, THREADS, 0, c->stream>>>(M, N, K, A, ai, ak, B, ldb, bmap, C, ldc, cmap, alpha, beta, D,
                                                     ldd);
@@ -215,10 +230,12 @@ void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, cons
 }
 
 template void gemm_gram<double2>(fs_ctx*, int, int, int, const double2*, long, const int*, const double2*, long,
-                                 const int*, double2*, long, long, double, double);
+                                 const int*, double2*, long, long, double, double, int);
 template void gemm_gram<float2>(fs_ctx*, int, int, int, const float2*, long, const int*, const float2*, long,
-                                const int*, double2*, long, long, double, double);
+                                const int*, double2*, long, long, double, double, int);
 template void gemm_nn<double2, double2>(fs_ctx*, int, int, int, const double2*, long, long, const double2*, long,
-                                        const int*, double2*, long, const int*, double, double, const double2*, long);
+                                        const int*, double2*, long, const int*, double, double, const double2*, long,
+                                        int);
 template void gemm_nn<float2, double2>(fs_ctx*, int, int, int, const double2*, long, long, const float2*, long,
-                                       const int*, float2*, long, const int*, double, double, const float2*, long);
+                                       const int*, float2*, long, const int*, double, double, const float2*, long,
+                                       int);

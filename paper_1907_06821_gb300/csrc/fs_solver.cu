@@ -48,7 +48,7 @@ void swapb(dbuf& a, dbuf& b) {
 }
 
 struct Small {
-    dbuf GA, GB, evals, work, info, theta, act, resid, dots, nrm, shift;
+    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale;
     int lwork = 0;
     int nbmax = 0;
 };
@@ -62,6 +62,48 @@ __global__ void shift_kernel(const double* ev, double e, double* out, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = ev[i] - e;
 }
+
+// d_i = 1 / sqrt(Re GB_ii)
+__global__ void diag_invsqrt_kernel(const double2* GB, int n, double* d) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        double g = GB[(long)i * n + i].x;
+        d[i] = g > 0 ? rsqrt(g) : 0.0;
+    }
+}
+
+// G_ij *= d_i d_j for both matrices
+__global__ void sym_scale_kernel(double2* GA, double2* GB, int n, const double* d) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    int i = (int)(t % n), j = (int)(t / n);
+    double f = d[i] * d[j];
+    GA[t].x *= f;
+    GA[t].y *= f;
+    GB[t].x *= f;
+    GB[t].y *= f;
+}
+
+// column j of T (n x k, ld n) *= 1 / sqrt(lam[j])
+__global__ void col_invsqrt_kernel(double2* T, int n, int k, const double* lam) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * k) return;
+    int j = (int)(t / n);
+    double f = rsqrt(lam[j]);
+    T[t].x *= f;
+    T[t].y *= f;
+}
+
+// row i of C (n x m, ld n) *= d[i]
+__global__ void row_scale_kernel(double2* C, int n, int m, const double* d) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * m) return;
+    int i = (int)(t % n);
+    C[t].x *= d[i];
+    C[t].y *= d[i];
+}
+
+inline int nblk(long total) { return (int)((total + 255) / 256); }
 
 struct Solver {
     fs_ctx* c;
@@ -82,6 +124,9 @@ struct Solver {
         s.nbmax = nbmax;
         s.GA.alloc((size_t)nbmax * nbmax * sizeof(double2));
         s.GB.alloc((size_t)nbmax * nbmax * sizeof(double2));
+        s.T1.alloc((size_t)nbmax * nbmax * sizeof(double2));
+        s.T2.alloc((size_t)nbmax * nbmax * sizeof(double2));
+        s.dscale.alloc(nbmax * sizeof(double));
         s.evals.alloc(nbmax * sizeof(double));
         s.info.alloc(sizeof(int));
         s.theta.alloc(nbmax * sizeof(double));
@@ -102,6 +147,7 @@ struct Solver {
 
     // generalized Hermitian eigenproblem GA c = lambda GB c, n x n column-major; returns info
     int hegvd(int n) {
+        ProfScope ps(c, KS_DENSE_LA, 0.0, 0.0);
         FS_SOLVER(cusolverDnZhegvd(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
                                    s.GA.as<cuDoubleComplex>(), n, s.GB.as<cuDoubleComplex>(), n, s.evals.as<double>(),
                                    s.work.as<cuDoubleComplex>(), s.lwork, s.info.as<int>()));
@@ -110,15 +156,69 @@ struct Solver {
         FS_CUDA(cudaStreamSynchronize(c->stream));
         return info;
     }
-    int heevd(int n) {
+    int heevd(int n, double2* A = nullptr) {
+        if (!A) A = s.GA.as<double2>();
+        ProfScope ps(c, KS_DENSE_LA, 0.0, 0.0);
         FS_SOLVER(cusolverDnZheevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                   s.GA.as<cuDoubleComplex>(), n, s.evals.as<double>(), s.work.as<cuDoubleComplex>(),
+                                   (cuDoubleComplex*)A, n, s.evals.as<double>(), s.work.as<cuDoubleComplex>(),
                                    s.lwork, s.info.as<int>()));
         int info = 0;
         FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaStreamSynchronize(c->stream));
         return info;
     }
+
+    // Rayleigh-Ritz of A on a basis of nb vectors with Gram matrices GA = <S, AS>
+    // and GB = <S, S> (column-major in s.GA, s.GB).  On return s.GA holds the
+    // nb x m coefficients of the m lowest Ritz vectors (column j = vector j)
+    // and s.evals[0..m) their Ritz values.  robust = true selects the basis
+    // by an eigendecomposition of the diagonally scaled GB, dropping the
+    // directions whose eigenvalue is below tau * max (near-dependent vectors
+    // in FP32), instead of a Cholesky factorisation of GB.  Returns the
+    // cuSOLVER info (0 = success).
+    int rr_basis(int nb, bool robust, double tau) {
+        double2* GA = s.GA.as<double2>();
+        double2* GB = s.GB.as<double2>();
+        if (!robust) return hegvd(nb);
+        diag_invsqrt_kernel<<<nblk(nb), 256, 0, c->stream>>>(GB, nb, s.dscale.as<double>());
+        sym_scale_kernel<<<nblk((long)nb * nb), 256, 0, c->stream>>>(GA, GB, nb, s.dscale.as<double>());
+        int info = heevd(nb, GB);
+        if (info != 0) return info;
+        std::vector<double> lam(nb);
+        FS_CUDA(cudaMemcpyAsync(lam.data(), s.evals.p, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        double lmax = lam[nb - 1];
+        int k = 0;
+        for (int i = nb - 1; i >= 0 && lam[i] > tau * lmax; --i) ++k;
+        if (k < m) return -1;
+        double2* T = GB + (long)(nb - k) * nb;  // kept eigenvectors, nb x k
+        col_invsqrt_kernel<<<nblk((long)nb * k), 256, 0, c->stream>>>(T, nb, k, s.evals.as<double>() + (nb - k));
+        const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
+        double2* tmp = s.T1.as<double2>();
+        double2* GAp = s.T2.as<double2>();
+        {
+        ProfScope ps(c, KS_DENSE_LA, 0.0, 8.0 * nb * (double)nb * k + 8.0 * k * (double)k * nb);
+        FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, k, nb, &one, (cuDoubleComplex*)GA, nb,
+                            (cuDoubleComplex*)T, nb, &zero, (cuDoubleComplex*)tmp, nb));
+        FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_C, CUBLAS_OP_N, k, k, nb, &one, (cuDoubleComplex*)T, nb,
+                            (cuDoubleComplex*)tmp, nb, &zero, (cuDoubleComplex*)GAp, k));
+        }
+        info = heevd(k, GAp);
+        if (info != 0) return info;
+        {
+        ProfScope ps(c, KS_DENSE_LA, 0.0, 8.0 * nb * (double)m * k);
+        FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, m, k, &one, (cuDoubleComplex*)T, nb,
+                            (cuDoubleComplex*)GAp, k, &zero, (cuDoubleComplex*)GA, nb));
+        }
+        row_scale_kernel<<<nblk((long)nb * m), 256, 0, c->stream>>>(GA, nb, m, s.dscale.as<double>());
+        FS_CUDA(cudaGetLastError());
+        last_kept = k;
+        return 0;
+    }
+    int last_kept = 0;
+
+    template <typename T2> static constexpr bool is_fp32() { return sizeof(T2) == 8; }
+    template <typename T2> static double tau_for() { return sizeof(T2) == 8 ? 1e-6 : 1e-11; }
 
     // Gram matrix of the basis blocks into G (nb x nb column-major): G(i, j) = <S_i, T_j>
     template <typename T2>
@@ -142,8 +242,9 @@ struct Solver {
         double2* GB = s.GB.as<double2>();
         gemm_gram<T2>(c, m, m, c->npw, Y, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
         gemm_gram<T2>(c, m, m, c->npw, X, c->npw, nullptr, X, c->npw, nullptr, GB, 1, m, 1.0, 0.0);
-        int info = hegvd(m);
-        if (info != 0) throw fs_error(FS_ERR_NUMERIC, "start block is rank deficient (hegvd info " + std::to_string(info) + ")");
+        int info = rr_basis(m, is_fp32<T2>(), tau_for<T2>());
+        if (info != 0) info = rr_basis(m, true, tau_for<T2>());
+        if (info != 0) throw fs_error(FS_ERR_NUMERIC, "start block is rank deficient (info " + std::to_string(info) + ")");
         rotate_simple(B, m);
         FS_CUDA(cudaMemcpyAsync(s.theta.p, s.evals.p, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         B.haveP = false;
@@ -169,6 +270,8 @@ struct Solver {
         std::vector<double> r(m);
         FS_CUDA(cudaMemcpyAsync(r.data(), s.resid.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaStreamSynchronize(c->stream));
+        ctx_check_errflag(c);
+        prof_flush(c);
         return r;
     }
 
@@ -214,7 +317,12 @@ struct Solver {
             int nb = m + na + (useP ? na : 0);
             gram_blocks<T2>(GA, nb, S, SZ, maps, sizes, offs, nblk);
             gram_blocks<T2>(GB, nb, S, S, maps, sizes, offs, nblk);
-            int info = hegvd(nb);
+            int info = rr_basis(nb, is_fp32<T2>(), tau_for<T2>());
+            if (info != 0 && !is_fp32<T2>()) {
+                gram_blocks<T2>(GA, nb, S, SZ, maps, sizes, offs, nblk);
+                gram_blocks<T2>(GB, nb, S, S, maps, sizes, offs, nblk);
+                info = rr_basis(nb, true, tau_for<T2>());
+            }
             if (info != 0) {
                 if (useP) {
                     useP = false;
@@ -224,7 +332,7 @@ struct Solver {
                                                    std::to_string(info) + ")");
             }
             // rotation: Pn = W Vw + P Vp ; Xn = X Vx + Pn  (and the same for Y, Z)
-            const double2* V = s.GA.as<double2>();
+            const double2* V = s.GA.as<double2>();  // nb x m coefficients
             const T2* srcX[3] = {X, Y, Z};
             const T2* srcW[3] = {W, YW, ZW};
             const T2* srcP[3] = {P, YP, ZP};
@@ -255,10 +363,12 @@ struct Solver {
     // Run block iterations until the nstates lowest bands have r <= tol, the
     // cap is reached, or (stall_check) the largest residual stops improving.
     template <typename T2>
-    int run(Blocks<T2>& B, int maxit, double target, bool stall_check, int& iters_done, double& worst) {
+    int run(Blocks<T2>& B, int maxit, double target, bool stall_check, int& iters_done, double& worst,
+            int restart_every = 0) {
         double best = 1e300;
         int since_best = 0;
         for (int it = 0;; ++it) {
+            if (restart_every > 0 && it > 0 && it % restart_every == 0) init_block<T2>(B);
             std::vector<double> r = residuals(B);
             worst = 0;
             for (int i = 0; i < nstates; ++i) worst = std::max(worst, std::isfinite(r[i]) ? r[i] : 1e300);
@@ -351,7 +461,7 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         B32.alloc(m, npw);
         vec_convert<double2, float2>(c, x0.as<double2>(), B32.X.as<float2>(), (size_t)m * npw);
         S.init_block<float2>(B32);
-        status = S.run<float2>(B32, c->opt.maxit, tol, true, iters, worst);
+        status = S.run<float2>(B32, c->opt.maxit, tol, true, iters, worst, 10);
         iters_mixed = iters;
         // carry the bands to FP64 (through x0, so that both block sets never coexist)
         vec_convert<float2, double2>(c, B32.X.as<float2>(), x0.as<double2>(), (size_t)m * npw);
