@@ -32,54 +32,72 @@ def _inner(a, b):
     return np.vdot(a, b)
 
 
-def cholesky_orthonormalise(X, *others):
-    """X <- X L^-H with S = X^H X = L L^H (rows of X are bands).
-    The same transform is applied to each block in ``others``."""
-    S = X.conj() @ X.T                    # S_ij = <x_i, x_j>
-    S = 0.5 * (S + S.conj().T)
-    Lc = np.linalg.cholesky(S)            # S = L L^H
-    T = np.linalg.inv(Lc).conj().T        # columns: new_j = sum_i x_i T_ij
-    out = [T.T @ X] + [T.T @ O for O in others]
-    return out
-
-
-def rayleigh_ritz_A(X, Y, Z):
-    """RR on A = (H-E)^2 in span X (orthonormal): G = Y^H Y, G = U diag(theta) U^H."""
-    G = Y.conj() @ Y.T
-    G = 0.5 * (G + G.conj().T)
-    theta, U = np.linalg.eigh(G)
-    return U.T @ X, U.T @ Y, U.T @ Z, theta
-
-
 def precond_M(kin, e_ref, dE):
     return 1.0 / ((kin - e_ref) ** 2 + dE * dE)
 
 
-def _orthonormalise_block(Wb, *others):
-    """Cholesky QR of one block (rows are vectors); None when its Gram
-    matrix is not numerically positive definite."""
-    S = Wb.conj() @ Wb.T
-    S = 0.5 * (S + S.conj().T)
-    try:
-        Lc = np.linalg.cholesky(S)
-    except np.linalg.LinAlgError:
-        return None
-    T = np.linalg.inv(Lc).conj().T
-    return [T.T @ Wb] + [T.T @ O for O in others]
+def rayleigh_ritz_basis(S, SY, m, tau):
+    """Rayleigh-Ritz of A on the rows of S (possibly near-dependent).
+
+    G_A = <S, A S> taken as <(H-E)S, (H-E)S> = SY^H SY (SY = (H-E)S), the
+    form that keeps the small Rayleigh quotients of A accurate in low
+    precision; G_B = <S, S>.  The basis is first scaled to unit norm
+    (D = diag(G_B)^-1/2), then orthonormalised through the eigenvectors of
+    D G_B D, dropping every direction whose eigenvalue is <= tau times the
+    largest (near-dependent vectors); the m lowest eigenpairs of the reduced
+    G_A give the Ritz values theta and the coefficients C (rows of S -> new
+    vectors, shape [len(S)][m]).
+    """
+    GA = SY.conj() @ SY.T
+    GB = S.conj() @ S.T
+    GA = 0.5 * (GA + GA.conj().T)
+    GB = 0.5 * (GB + GB.conj().T)
+    d = 1.0 / np.sqrt(np.real(np.diag(GB)))
+    lam, U = np.linalg.eigh(d[:, None] * GB * d[None, :])
+    keep = lam > tau * lam.max()
+    T = (d[:, None] * U[:, keep]) / np.sqrt(lam[keep])[None, :]
+    ga = T.conj().T @ GA @ T
+    theta, Cr = np.linalg.eigh(0.5 * (ga + ga.conj().T))
+    return theta[:m], T @ Cr[:, :m]
+
+
+def residual_tolerance_A(theta, tol):
+    """Per-band threshold on the A residual ||A x - theta x|| that matches an
+    H residual of about tol: for an isolated eigenvector of H at distance
+    d = sqrt(theta) from E the A residual is about 2 d times the H residual;
+    the factor is floored at 1e-3 for states that sit on E."""
+    return tol * np.maximum(np.sqrt(np.maximum(theta, 0.0)), 1e-3)
+
+
+def h_ritz_check(X, Y, theta, E, nstates):
+    """Rayleigh-Ritz step on H within the nstates lowest A-Ritz vectors (plus
+    any band tied with the nstates-th within 1e-3 relative in theta): H-Ritz
+    values eps, vectors and their H residuals ||H u - eps u||, nstates nearest
+    E first (ordered by (|eps - E|, eps))."""
+    n = nstates + int(np.sum(theta[nstates:] <= theta[nstates - 1] * (1.0 + 1e-3)))
+    Hs = X[:n].conj() @ Y[:n].T
+    lam, U = np.linalg.eigh(0.5 * (Hs + Hs.conj().T))
+    Xr = U.T @ X[:n]
+    Yr = U.T @ Y[:n]
+    res = np.linalg.norm(Yr - lam[:, None] * Xr, axis=1)
+    eps = lam + E
+    order = np.lexsort((eps, np.abs(eps - E)))[:nstates]
+    return eps[order], Xr[order], res[order]
 
 
 def solve_folded(w, e_ref, nstates, tol, x0_raw, guard=None, dE=0.5, maxit=3000,
-                 ham=None, callback=None, precond=None):
-    """Folded-spectrum all-band PCG in its locally-optimal block form.
+                 ham=None, callback=None, precond=None, tau=1e-10):
+    """Folded-spectrum all-band PCG in its locally optimal block form.
 
     Each iteration minimises the Rayleigh quotient of A = (H-E)^2 over
-    span{X, W, P}: X the current bands, W = M(R) the preconditioned residuals
-    R = A X - X Theta (made orthogonal to X), P the previous update
-    directions (made orthogonal to X and W).  The Ritz vectors of the m lowest
-    Ritz values of A become the new bands.  A band counts as converged when
-    its H residual ||y - <x,y> x|| (y = (H-E) x) is <= tol; the run stops when
-    the nstates lowest bands have converged, then a Rayleigh-Ritz step on H
-    in span X gives the eigenvalues.
+    span{X, W, P}: X the current m bands (A-Ritz vectors, Ritz values theta),
+    W = M(R) the preconditioned A residuals R = A X - X Theta of the bands that
+    are not yet converged (made orthogonal to X), P their previous update
+    directions (made orthogonal to X).  The Rayleigh-Ritz step selects its
+    basis robustly (rayleigh_ritz_basis).  Convergence: once every wanted band
+    (the nstates lowest theta) has an A residual below residual_tolerance_A, a
+    Rayleigh-Ritz step on H within those bands (h_ritz_check) must give H
+    residuals <= tol for the nstates pairs nearest E.
 
     Returns dict(eps, X, resid, iters, converged, theta, napply), eps ordered
     by (|eps - e_ref|, eps) and X[nstates][npw] the matching states.
@@ -89,63 +107,55 @@ def solve_folded(w, e_ref, nstates, tol, x0_raw, guard=None, dE=0.5, maxit=3000,
     E = e_ref
     M = precond_M(h.kin, E, dE) if precond is None else precond
     X = x0_raw[:m] * (1.0 / (1.0 + h.kin))[None, :]
-    (X,) = cholesky_orthonormalise(X)
     Y = h.apply(X, E)
     Z = h.apply(Y, E)                          # Z = A X
-    X, Y, Z, theta = rayleigh_ritz_A(X, Y, Z)
+    theta, C = rayleigh_ritz_basis(X, Y, m, tau)
+    X, Y, Z = C.T @ X, C.T @ Y, C.T @ Z
     P = YP = ZP = None
     converged = False
     it = 0
+    eps = states = res = None
     for it in range(0, maxit + 1):
-        resid = np.array([np.linalg.norm(Y[i] - _inner(X[i], Y[i]) * X[i]) for i in range(m)])
+        R = Z - theta[:, None] * X
+        ra = np.linalg.norm(R, axis=1)
+        tolA = residual_tolerance_A(theta, tol)
         if callback is not None:
-            callback(it, theta, resid)
-        if np.all(resid[:nstates] <= tol):
-            converged = True
-            break
+            callback(it, theta, ra)
+        if np.all(ra[:nstates] <= tolA[:nstates]):
+            eps, states, res = h_ritz_check(X, Y, theta, E, nstates)
+            if np.all(res <= tol):
+                converged = True
+                break
         if it == maxit:
             break
-        R = Z - theta[:, None] * X
-        W = M[None, :] * R
+        act = np.where(ra > tolA)[0]
+        if act.size == 0:
+            act = np.arange(m)
+        W = M[None, :] * R[act]
         W = W - (X.conj() @ W.T).T @ X
-        ow = _orthonormalise_block(W)
-        if ow is None:
-            break
-        (W,) = ow
+        W = W / np.linalg.norm(W, axis=1)[:, None]
         YW = h.apply(W, E)
         ZW = h.apply(YW, E)
         blocks = [(X, Y, Z), (W, YW, ZW)]
         if P is not None:
-            cx = X.conj() @ P.T                 # <x_i, p_j>
-            cw = W.conj() @ P.T
-            P = P - cx.T @ X - cw.T @ W
-            YP = YP - cx.T @ Y - cw.T @ YW
-            ZP = ZP - cx.T @ Z - cw.T @ ZW
-            op = _orthonormalise_block(P, YP, ZP)
-            if op is not None:
-                P, YP, ZP = op
-                blocks.append((P, YP, ZP))
+            Pa, YPa, ZPa = P[act], YP[act], ZP[act]
+            cx = X.conj() @ Pa.T                 # <x_i, p_j>
+            Pa = Pa - cx.T @ X
+            YPa = YPa - cx.T @ Y
+            ZPa = ZPa - cx.T @ Z
+            nrm = np.linalg.norm(Pa, axis=1)
+            blocks.append((Pa / nrm[:, None], YPa / nrm[:, None], ZPa / nrm[:, None]))
         S = np.concatenate([b[0] for b in blocks])
         SY = np.concatenate([b[1] for b in blocks])
         SZ = np.concatenate([b[2] for b in blocks])
-        GA = S.conj() @ SZ.T
-        GB = S.conj() @ S.T
-        GA = 0.5 * (GA + GA.conj().T)
-        GB = 0.5 * (GB + GB.conj().T)
-        theta, C = sla.eigh(GA, GB, subset_by_index=[0, m - 1])
+        theta, C = rayleigh_ritz_basis(S, SY, m, tau)
         Cp = C.copy()
         Cp[:m] = 0.0
         P, YP, ZP = Cp.T @ S, Cp.T @ SY, Cp.T @ SZ
         X = C[:m].T @ X + P
         Y = C[:m].T @ Y + YP
         Z = C[:m].T @ Z + ZP
-    # final Rayleigh-Ritz on H in span X
-    Hs = X.conj() @ Y.T + E * np.eye(m)
-    Hs = 0.5 * (Hs + Hs.conj().T)
-    eps, U = np.linalg.eigh(Hs)
-    X = U.T @ X
-    Y = U.T @ Y
-    res_all = np.array([np.linalg.norm(Y[i] - (eps[i] - E) * X[i]) for i in range(m)])
-    order = np.lexsort((eps, np.abs(eps - E)))[:nstates]
-    return dict(eps=eps[order], X=X[order], resid=res_all[order], iters=it,
-                converged=converged, theta=theta, napply=h.napply)
+    if eps is None or not converged:
+        eps, states, res = h_ritz_check(X, Y, theta, E, nstates)
+    return dict(eps=eps, X=states, resid=res, iters=it, converged=converged, theta=theta,
+                napply=h.napply)

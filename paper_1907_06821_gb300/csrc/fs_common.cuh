@@ -190,6 +190,7 @@ struct fs_ctx {
     dbuf projbuf;     // [nb][nptot] complex (P)
     dbuf projbuf2;    // [nb][nptot] complex (Q = D P)
     dbuf splitk;      // split-K partial sums
+    dbuf coefbuf;     // float2 coefficients of the tensor-core apply form
 
     // solver state
     dbuf init_states; // double2 [ninit][npw]
@@ -201,6 +202,8 @@ struct fs_ctx {
     Prof prof;
     dbuf errflag;     // int: set by a device-side wait that gave up
     int gemm_path = 0;
+    int tc_gram_kchunk = 1 << 30;  // complex k per tensor-memory accumulation (Gram form)
+    int tc_nn_kchunk = 1 << 30;    // complex k per tensor-memory accumulation (apply form)
     std::string err;
 };
 
@@ -248,8 +251,12 @@ void ctx_check_errflag(fs_ctx* c);
 // vector kernels (fs_vec.cu)
 template <typename T2> void vec_resid(fs_ctx* c, const T2* X, const T2* Y, int m, double* resid, double2* dot);
 template <typename T2>
-void vec_make_w(fs_ctx* c, const T2* X, const T2* Z, const double* theta, const int* act, int na, T2* W, double e_ref,
-                double dE, int precond, const double* band_kin);
+void vec_make_w(fs_ctx* c, const T2* R, const int* act, int na, T2* W, double e_ref, double dE, int precond,
+                const double* band_kin);
+template <typename T2> void vec_rh(fs_ctx* c, const T2* X, const T2* Y, const double2* dots, int m, T2* RH);
+template <typename T2>
+void vec_a_resid(fs_ctx* c, const T2* ZR, T2* RH, const T2* X, const double2* dots, const double* theta, int m,
+                 double* ra);
 template <typename T2> void vec_row_norms(fs_ctx* c, const T2* X, const int* map, int nrows, double* out);
 template <typename T2> void vec_scale_rows(fs_ctx* c, T2* X, const int* map, int nrows, const double* nrm);
 template <typename T2>

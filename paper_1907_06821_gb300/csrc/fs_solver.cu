@@ -1,20 +1,23 @@
 // Folded-spectrum all-band PCG (locally optimal block form) on the GPU.
 //
 // Operator A = (H - E)^2 (paper Sec. II.C, Eq. wl1); its lowest eigenvectors
-// are the eigenvectors of H nearest E.  Per iteration, for the m bands X with
-// Y = (H-E)X, Z = AX (all kept on the device):
-//   r_i  = || y_i - <x_i,y_i> x_i ||              H residual (convergence test)
-//   act  = bands with r_i > tol                    (soft locking)
-//   W    = M (Z - X Theta) on act, W -= X (X^H W), rows normalised
-//   YW   = (H-E) W, ZW = (H-E) YW                  two H applications
+// are the eigenvectors of H nearest E.  State: m bands X (A-Ritz vectors, Ritz
+// values theta) and their images Y = (H-E)X.  Per iteration:
+//   d_i = <x_i, y_i>, r_i = y_i - d_i x_i       H residual vectors (all bands)
+//   R_i = (H-E) r_i + d_i r_i + (d_i^2 - theta_i) x_i   = A x_i - theta_i x_i
+//        (one H application per band; every term scales with ||r_i||, so the
+//         A residual stays accurate in FP32 down to the FP32 noise of r_i)
+//   act  = bands whose ||R_i|| is above the threshold matching an H residual tol
+//   W    = M R on act, W -= X (X^H W), rows normalised, YW = (H-E) W
 //   P    = previous directions on act, made orthogonal to X, normalised
-//   Rayleigh-Ritz of A on S = [X W P]: G_A c = theta G_B c (FP64, cuSOLVER)
-//   X <- S c (lowest m), P <- [W P] c_WP; same for Y and Z by linearity.
-// Finally a Rayleigh-Ritz step on H in span X gives eps and the states.
-// Mixed precision: the vectors, FFTs and GEMMs run in FP32 with FP64 small
-// dense algebra until the FP32 residuals reach tol (or stall); the bands are
-// then carried to FP64 and the same iteration continues in FP64 until the
-// FP64 residuals reach tol.
+//   Rayleigh-Ritz of A on S = [X W P]: G_A = ((H-E)S)^H (H-E)S, G_B = S^H S,
+//   robust basis selection (FP64 dense eigensolves);
+//   X <- S c (lowest m), P <- [W P] c_WP; Y, YP by linearity.
+// Convergence: a Rayleigh-Ritz step on H within the wanted bands; their H
+// residuals must be <= tol for the nstates pairs nearest E.
+// Mixed precision: vectors, FFTs and GEMMs in FP32 (tensor-core TF32 x3),
+// dense algebra in FP64, Y (and YP) recomputed every 10 iterations; then an
+// FP64 check of the wanted bands, and FP64 iterations only if it fails.
 #include "fs_common.cuh"
 
 #include <cuComplex.h>
@@ -30,15 +33,15 @@ void ctx_ensure_fp32(fs_ctx* c);
 namespace {
 
 template <typename T2> struct Blocks {
-    dbuf X, Y, Z, W, YW, ZW, P, YP, ZP, tX, tY, tZ, tP, tYP, tZP;
+    dbuf X, Y, W, YW, P, YP, RH, ZR, tX, tY, tP, tYP;
     bool haveP = false;
     void alloc(int m, long npw) {
         size_t b = (size_t)m * npw * sizeof(T2);
-        for (dbuf* d : {&X, &Y, &Z, &W, &YW, &ZW, &P, &YP, &ZP, &tX, &tY, &tZ, &tP, &tYP, &tZP}) d->alloc(b);
+        for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->alloc(b);
         haveP = false;
     }
     void free_all() {
-        for (dbuf* d : {&X, &Y, &Z, &W, &YW, &ZW, &P, &YP, &ZP, &tX, &tY, &tZ, &tP, &tYP, &tZP}) d->release();
+        for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->release();
     }
 };
 
@@ -104,6 +107,19 @@ __global__ void row_scale_kernel(double2* C, int n, int m, const double* d) {
 }
 
 inline int nblk(long total) { return (int)((total + 255) / 256); }
+inline int nblk_(long total) { return nblk(total); }
+
+// G(i, j) = conj(G(j, i)) where the block of i (boundaries b1 <= b2) is below the block of j
+__global__ void herm_fill_kernel(double2* G, int n, int b1, int b2) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * n) return;
+    int i = (int)(t % n), j = (int)(t / n);
+    int bi = (i >= b1) + (i >= b2), bj = (j >= b1) + (j >= b2);
+    if (bi < bj) {
+        double2 v = G[(long)i * n + j];
+        G[t] = make_double2(v.x, -v.y);
+    }
+}
 
 struct Solver {
     fs_ctx* c;
@@ -220,125 +236,189 @@ struct Solver {
     template <typename T2> static constexpr bool is_fp32() { return sizeof(T2) == 8; }
     template <typename T2> static double tau_for() { return sizeof(T2) == 8 ? 1e-6 : 1e-11; }
 
-    // Gram matrix of the basis blocks into G (nb x nb column-major): G(i, j) = <S_i, T_j>
+    // Hermitian Gram matrix of the basis blocks into G (nb x nb column-major):
+    // G(i, j) = <S_i, T_j> computed for row block >= column block (T = S or
+    // T = A S, both Hermitian forms), the upper blocks filled by conjugation.
     template <typename T2>
     void gram_blocks(double2* G, int nb, const T2* const* S, const T2* const* T, const int* const* maps,
                      const int* sizes, const int* offs, int nblk) {
         for (int I = 0; I < nblk; ++I)
-            for (int J = 0; J < nblk; ++J)
+            for (int J = 0; J <= I; ++J)
                 gemm_gram<T2>(c, sizes[I], sizes[J], c->npw, S[I], c->npw, maps[I], T[J], c->npw, maps[J],
                               G + offs[I] + (long)offs[J] * nb, 1, nb, 1.0, 0.0);
+        int b1 = nblk > 1 ? offs[1] : nb, b2 = nblk > 2 ? offs[2] : nb;
+        herm_fill_kernel<<<nblk_((long)nb * nb), 256, 0, c->stream>>>(G, nb, b1, b2);
+        FS_CUDA(cudaGetLastError());
     }
 
     // Initial Rayleigh-Ritz on A in span X (X need not be orthonormal).
     template <typename T2> void init_block(Blocks<T2>& B) {
         T2* X = B.X.template as<T2>();
         T2* Y = B.Y.template as<T2>();
-        T2* Z = B.Z.template as<T2>();
         HE(X, Y, m);
-        HE(Y, Z, m);
         ensure_small(3 * m);
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
         gemm_gram<T2>(c, m, m, c->npw, Y, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
         gemm_gram<T2>(c, m, m, c->npw, X, c->npw, nullptr, X, c->npw, nullptr, GB, 1, m, 1.0, 0.0);
-        int info = rr_basis(m, is_fp32<T2>(), tau_for<T2>());
-        if (info != 0) info = rr_basis(m, true, tau_for<T2>());
+        int info = rr_basis(m, true, tau_for<T2>());
         if (info != 0) throw fs_error(FS_ERR_NUMERIC, "start block is rank deficient (info " + std::to_string(info) + ")");
         rotate_simple(B, m);
         FS_CUDA(cudaMemcpyAsync(s.theta.p, s.evals.p, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         B.haveP = false;
     }
 
-    // X, Y, Z <- (X, Y, Z) V[:, :m] with V = GA (n x n, column-major)
+    // FP32 stage: the images Y (and YP) are carried by linear updates and
+    // drift from (H-E)X in FP32; recompute them from X and P, then redo the
+    // Rayleigh-Ritz step on X.  P is kept.
+    template <typename T2> void refresh(Blocks<T2>& B) {
+        bool keepP = B.haveP;
+        init_block<T2>(B);
+        if (keepP) {
+            HE(B.P.template as<T2>(), B.YP.template as<T2>(), m);
+            B.haveP = true;
+        }
+    }
+
+    // X, Y <- (X, Y) V[:, :m] with V = GA (n x n, column-major)
     template <typename T2> void rotate_simple(Blocks<T2>& B, int n) {
         const double2* V = s.GA.as<double2>();
-        dbuf* src[3] = {&B.X, &B.Y, &B.Z};
-        dbuf* dst[3] = {&B.tX, &B.tY, &B.tZ};
-        for (int q = 0; q < 3; ++q)
+        dbuf* src[2] = {&B.X, &B.Y};
+        dbuf* dst[2] = {&B.tX, &B.tY};
+        for (int q = 0; q < 2; ++q)
             gemm_nn<T2, double2>(c, m, c->npw, n, V, n, 1, src[q]->template as<T2>(), c->npw, nullptr,
                                  dst[q]->template as<T2>(), c->npw, nullptr, 1.0, 0.0, nullptr, 0);
         swapb(B.X, B.tX);
         swapb(B.Y, B.tY);
-        swapb(B.Z, B.tZ);
     }
 
-    // Residuals of all bands; returns them on the host.
-    template <typename T2> std::vector<double> residuals(Blocks<T2>& B) {
-        vec_resid<T2>(c, B.X.template as<T2>(), B.Y.template as<T2>(), m, s.resid.as<double>(),
-                      s.dots.as<double2>());
-        std::vector<double> r(m);
-        FS_CUDA(cudaMemcpyAsync(r.data(), s.resid.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    // A residuals R_i = A x_i - theta_i x_i of all bands (left in B.RH), their
+    // norms and the Ritz values on the host.  Costs one H application per band.
+    template <typename T2> void a_residuals(Blocks<T2>& B, std::vector<double>& ra, std::vector<double>& th) {
+        T2* X = B.X.template as<T2>();
+        T2* Y = B.Y.template as<T2>();
+        T2* RH = B.RH.template as<T2>();
+        T2* ZR = B.ZR.template as<T2>();
+        vec_resid<T2>(c, X, Y, m, s.resid.as<double>(), s.dots.as<double2>());
+        vec_rh<T2>(c, X, Y, s.dots.as<double2>(), m, RH);
+        HE(RH, ZR, m);
+        vec_a_resid<T2>(c, ZR, RH, X, s.dots.as<double2>(), s.theta.as<double>(), m, s.resid.as<double>());
+        ra.resize(m);
+        th.resize(m);
+        FS_CUDA(cudaMemcpyAsync(ra.data(), s.resid.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaMemcpyAsync(th.data(), s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaStreamSynchronize(c->stream));
         ctx_check_errflag(c);
         prof_flush(c);
-        return r;
     }
 
-    // One block iteration on the active set; returns false if the basis broke down.
+    // Threshold on the A residual matching an H residual of about tol: for an
+    // isolated eigenvector at distance d = sqrt(theta) from E the A residual is
+    // about 2 d times the H residual (factor floored at 1e-3).
+    double tol_a(double theta, double target) const { return target * std::max(std::sqrt(std::max(theta, 0.0)), 1e-3); }
+
+    // Rayleigh-Ritz on H within the wanted A-Ritz vectors (the nstates lowest
+    // theta plus bands tied with the nstates-th within 1e-3): H-Ritz pairs and
+    // their H residuals.  The rotated vectors are left in B.tX (rows 0..n).
+    // Outputs: n, eps (E + Ritz values of H - E), res, and order (the nstates
+    // pairs nearest E by (|eps - E|, eps)).
+    template <typename T2>
+    void h_ritz(Blocks<T2>& B, const std::vector<double>& th, int& n, std::vector<double>& eps,
+                std::vector<double>& res, std::vector<int>& order) {
+        n = nstates;
+        while (n < m && th[n] <= th[nstates - 1] * (1.0 + 1e-3)) ++n;
+        T2* X = B.X.template as<T2>();
+        T2* Y = B.Y.template as<T2>();
+        double2* GA = s.GA.as<double2>();
+        double2* GB = s.GB.as<double2>();
+        // generalized form with the overlap <x_i, x_j>: the Ritz vectors come out
+        // orthonormal in the working precision even when X came from the FP32 stage
+        gemm_gram<T2>(c, n, n, c->npw, X, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, n, 1.0, 0.0);
+        gemm_gram<T2>(c, n, n, c->npw, X, c->npw, nullptr, X, c->npw, nullptr, GB, 1, n, 1.0, 0.0);
+        int info = hegvd(n);
+        if (info != 0) throw fs_error(FS_ERR_NUMERIC, "Rayleigh-Ritz on H failed (info " + std::to_string(info) + ")");
+        const double2* U = s.GA.as<double2>();
+        gemm_nn<T2, double2>(c, n, c->npw, n, U, n, 1, X, c->npw, nullptr, B.tX.template as<T2>(), c->npw, nullptr,
+                             1.0, 0.0, nullptr, 0);
+        gemm_nn<T2, double2>(c, n, c->npw, n, U, n, 1, Y, c->npw, nullptr, B.tY.template as<T2>(), c->npw, nullptr,
+                             1.0, 0.0, nullptr, 0);
+        vec_resid_shift<T2>(c, B.tX.template as<T2>(), B.tY.template as<T2>(), s.evals.as<double>(), n,
+                            s.resid.as<double>());
+        std::vector<double> lam(n);
+        res.resize(n);
+        FS_CUDA(cudaMemcpyAsync(lam.data(), s.evals.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaMemcpyAsync(res.data(), s.resid.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        eps.resize(n);
+        for (int i = 0; i < n; ++i) eps[i] = lam[i] + E;
+        order.resize(n);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            double da = std::fabs(eps[a] - E), db = std::fabs(eps[b] - E);
+            if (da != db) return da < db;
+            return eps[a] < eps[b];
+        });
+        order.resize(nstates);
+    }
+
+    // One block iteration on the active set (B.RH holds the A residuals of all bands).
     template <typename T2> void iterate(Blocks<T2>& B, const std::vector<int>& act_h) {
         const int na = (int)act_h.size();
         const long npw = c->npw;
         int* act = s.act.as<int>();
         FS_CUDA(cudaMemcpyAsync(act, act_h.data(), na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-        T2 *X = B.X.template as<T2>(), *Y = B.Y.template as<T2>(), *Z = B.Z.template as<T2>();
-        T2 *W = B.W.template as<T2>(), *YW = B.YW.template as<T2>(), *ZW = B.ZW.template as<T2>();
-        T2 *P = B.P.template as<T2>(), *YP = B.YP.template as<T2>(), *ZP = B.ZP.template as<T2>();
+        T2 *X = B.X.template as<T2>(), *Y = B.Y.template as<T2>();
+        T2 *W = B.W.template as<T2>(), *YW = B.YW.template as<T2>();
+        T2 *P = B.P.template as<T2>(), *YP = B.YP.template as<T2>();
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
-        // W = M (Z - X Theta), made orthogonal to X and normalised
-        vec_make_w<T2>(c, X, Z, s.theta.as<double>(), act, na, W, E, c->opt.dE,
+        // W = M R on the active bands, made orthogonal to X and normalised
+        vec_make_w<T2>(c, B.RH.template as<T2>(), act, na, W, E, c->opt.dE,
                        c->opt.precond == FS_PREC_TETER ? 1 : 0, nullptr);
         gemm_gram<T2>(c, m, na, npw, X, npw, nullptr, W, npw, nullptr, GB, 1, m, 1.0, 0.0);
         gemm_nn<T2, double2>(c, na, npw, m, GB, m, 1, X, npw, nullptr, W, npw, nullptr, -1.0, 1.0, W, npw);
         vec_row_norms<T2>(c, W, nullptr, na, s.nrm.as<double>());
         vec_scale_rows<T2>(c, W, nullptr, na, s.nrm.as<double>());
         HE(W, YW, na);
-        HE(YW, ZW, na);
         bool useP = B.haveP;
         if (useP) {
-            // P[act] -= X (X^H P[act]); same combination for YP, ZP; then normalise
+            // P[act] -= X (X^H P[act]); the same combination for YP; then normalise
             gemm_gram<T2>(c, m, na, npw, X, npw, nullptr, P, npw, act, GB, 1, m, 1.0, 0.0);
             gemm_nn<T2, double2>(c, na, npw, m, GB, m, 1, X, npw, nullptr, P, npw, act, -1.0, 1.0, P, npw);
             gemm_nn<T2, double2>(c, na, npw, m, GB, m, 1, Y, npw, nullptr, YP, npw, act, -1.0, 1.0, YP, npw);
-            gemm_nn<T2, double2>(c, na, npw, m, GB, m, 1, Z, npw, nullptr, ZP, npw, act, -1.0, 1.0, ZP, npw);
             vec_row_norms<T2>(c, P, act, na, s.nrm.as<double>());
             vec_scale_rows<T2>(c, P, act, na, s.nrm.as<double>());
             vec_scale_rows<T2>(c, YP, act, na, s.nrm.as<double>());
-            vec_scale_rows<T2>(c, ZP, act, na, s.nrm.as<double>());
         }
         for (int attempt = 0; attempt < 2; ++attempt) {
             int nblk = useP ? 3 : 2;
             const T2* S[3] = {X, W, P};
-            const T2* SZ[3] = {Z, ZW, ZP};
+            const T2* SY[3] = {Y, YW, YP};
             const int* maps[3] = {nullptr, nullptr, act};
             int sizes[3] = {m, na, na};
             int offs[3] = {0, m, m + na};
             int nb = m + na + (useP ? na : 0);
-            gram_blocks<T2>(GA, nb, S, SZ, maps, sizes, offs, nblk);
+            // <s_i, A s_j> = <(H-E)s_i, (H-E)s_j>: the Y images keep the small
+            // Rayleigh quotients of A accurate in the FP32 stage
+            gram_blocks<T2>(GA, nb, SY, SY, maps, sizes, offs, nblk);
             gram_blocks<T2>(GB, nb, S, S, maps, sizes, offs, nblk);
-            int info = rr_basis(nb, is_fp32<T2>(), tau_for<T2>());
-            if (info != 0 && !is_fp32<T2>()) {
-                gram_blocks<T2>(GA, nb, S, SZ, maps, sizes, offs, nblk);
-                gram_blocks<T2>(GB, nb, S, S, maps, sizes, offs, nblk);
-                info = rr_basis(nb, true, tau_for<T2>());
-            }
+            int info = rr_basis(nb, true, tau_for<T2>());
             if (info != 0) {
                 if (useP) {
                     useP = false;
                     continue;
                 }
-                throw fs_error(FS_ERR_NUMERIC, "Rayleigh-Ritz basis is not positive definite (info " +
+                throw fs_error(FS_ERR_NUMERIC, "Rayleigh-Ritz basis selection failed (info " +
                                                    std::to_string(info) + ")");
             }
-            // rotation: Pn = W Vw + P Vp ; Xn = X Vx + Pn  (and the same for Y, Z)
+            // rotation: Pn = W Vw + P Vp ; Xn = X Vx + Pn  (and the same for Y)
             const double2* V = s.GA.as<double2>();  // nb x m coefficients
-            const T2* srcX[3] = {X, Y, Z};
-            const T2* srcW[3] = {W, YW, ZW};
-            const T2* srcP[3] = {P, YP, ZP};
-            dbuf* dP[3] = {&B.tP, &B.tYP, &B.tZP};
-            dbuf* dX[3] = {&B.tX, &B.tY, &B.tZ};
-            for (int q = 0; q < 3; ++q) {
+            const T2* srcX[2] = {X, Y};
+            const T2* srcW[2] = {W, YW};
+            const T2* srcP[2] = {P, YP};
+            dbuf* dP[2] = {&B.tP, &B.tYP};
+            dbuf* dX[2] = {&B.tX, &B.tY};
+            for (int q = 0; q < 2; ++q) {
                 T2* pn = dP[q]->template as<T2>();
                 gemm_nn<T2, double2>(c, m, npw, na, V + m, nb, 1, srcW[q], npw, nullptr, pn, npw, nullptr, 1.0, 0.0,
                                      nullptr, 0);
@@ -350,76 +430,72 @@ struct Solver {
             }
             swapb(B.X, B.tX);
             swapb(B.Y, B.tY);
-            swapb(B.Z, B.tZ);
             swapb(B.P, B.tP);
             swapb(B.YP, B.tYP);
-            swapb(B.ZP, B.tZP);
             B.haveP = true;
             FS_CUDA(cudaMemcpyAsync(s.theta.p, s.evals.p, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
             return;
         }
     }
 
-    // Run block iterations until the nstates lowest bands have r <= tol, the
-    // cap is reached, or (stall_check) the largest residual stops improving.
+    // Block iterations until the H residuals of the nstates pairs nearest E
+    // are <= target (returns 1, results filled), the cap is reached (0), or,
+    // with stall_check, the wanted A residuals stop improving (2).
     template <typename T2>
-    int run(Blocks<T2>& B, int maxit, double target, bool stall_check, int& iters_done, double& worst,
-            int restart_every = 0) {
+    int run(Blocks<T2>& B, int maxit, double target, bool stall_check, int& iters_done, int refresh_every,
+            std::vector<double>& eps, std::vector<double>& res, std::vector<int>& order, int& nres) {
         double best = 1e300;
         int since_best = 0;
+        std::vector<double> ra, th;
         for (int it = 0;; ++it) {
-            if (restart_every > 0 && it > 0 && it % restart_every == 0) init_block<T2>(B);
-            std::vector<double> r = residuals(B);
-            worst = 0;
-            for (int i = 0; i < nstates; ++i) worst = std::max(worst, std::isfinite(r[i]) ? r[i] : 1e300);
-            if (!std::isfinite(worst) || worst >= 1e299)
-                throw fs_error(FS_ERR_NUMERIC, "NaN/Inf in the residuals");
+            if (refresh_every > 0 && it > 0 && it % refresh_every == 0) refresh<T2>(B);
+            a_residuals(B, ra, th);
+            double worst = 0;  // largest wanted A residual relative to its threshold
+            for (int i = 0; i < nstates; ++i) {
+                double q = ra[i] / tol_a(th[i], target);
+                if (!std::isfinite(q)) throw fs_error(FS_ERR_NUMERIC, "NaN/Inf in the residuals");
+                worst = std::max(worst, q);
+            }
+            double hworst = -1;
+            // the H check runs once every wanted A residual is below its threshold,
+            // and every 5 iterations once they are within 100x of it (the FP32 A
+            // residual has a noise floor that can keep the first gate shut)
+            // (in FP32 the A residual of states close to E carries the noise of the
+            // FP32 (H-E)x, so the H check itself also runs every 5 iterations)
+            if (worst <= 1.0 || (it % 5 == 0 && (worst <= 100.0 || is_fp32<T2>()))) {
+                h_ritz<T2>(B, th, nres, eps, res, order);
+                hworst = 0;
+                for (int i : order) hworst = std::max(hworst, res[i]);
+                if (hworst <= target) return 1;
+            }
             if (verbose)
-                fprintf(stderr, "[fs] it %d (%s) max resid %.3e\n", iters_done, sizeof(T2) == 16 ? "fp64" : "fp32",
-                        worst);
-            if (worst <= target) return 1;
+                fprintf(stderr, "[fs] it %d (%s) wanted A-residual/threshold %.3e  H-check %.3e\n", iters_done,
+                        is_fp32<T2>() ? "fp32" : "fp64", worst, hworst);
             if (it >= maxit) return 0;
             if (stall_check) {
-                if (worst < 0.7 * best) {
-                    best = worst;
+                // geometric mean of the wanted bands' excess over their thresholds:
+                // it keeps falling while the bulk of the block converges even when
+                // the hardest band sits on a plateau
+                double lg = 0;
+                for (int i = 0; i < nstates; ++i) lg += std::log(std::max(ra[i] / tol_a(th[i], target), 1.0));
+                double metric = std::exp(lg / nstates);
+                if (hworst >= 0) metric = hworst / target;
+                else if (best < 1e299 && it % 5 != 0) metric = best;  // judge on the H check when it runs
+                if (metric < 0.7 * best) {
+                    best = metric;
                     since_best = 0;
-                } else if (++since_best >= 15 && worst < 1e-3) {
+                } else if (++since_best >= 30) {
                     return 2;
                 }
             }
             std::vector<int> act;
             for (int i = 0; i < m; ++i)
-                if (r[i] > target) act.push_back(i);
-            if (act.empty()) return 1;
+                if (ra[i] > tol_a(th[i], target)) act.push_back(i);
+            if (act.empty())
+                for (int i = 0; i < m; ++i) act.push_back(i);
             iterate<T2>(B, act);
             ++iters_done;
         }
-    }
-
-    template <typename T2> void final_rr(Blocks<T2>& B, std::vector<double>& eps, std::vector<double>& res) {
-        T2* X = B.X.template as<T2>();
-        T2* Y = B.Y.template as<T2>();
-        double2* GA = s.GA.as<double2>();
-        gemm_gram<T2>(c, m, m, c->npw, X, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
-        add_diag_kernel<<<(m + 127) / 128, 128, 0, c->stream>>>(GA, m, E);
-        int info = heevd(m);
-        if (info != 0) throw fs_error(FS_ERR_NUMERIC, "final Rayleigh-Ritz failed (info " + std::to_string(info) + ")");
-        // rotate X, Y only
-        const double2* V = s.GA.as<double2>();
-        gemm_nn<T2, double2>(c, m, c->npw, m, V, m, 1, X, c->npw, nullptr, B.tX.template as<T2>(), c->npw, nullptr,
-                             1.0, 0.0, nullptr, 0);
-        gemm_nn<T2, double2>(c, m, c->npw, m, V, m, 1, Y, c->npw, nullptr, B.tY.template as<T2>(), c->npw, nullptr,
-                             1.0, 0.0, nullptr, 0);
-        swapb(B.X, B.tX);
-        swapb(B.Y, B.tY);
-        shift_kernel<<<(m + 127) / 128, 128, 0, c->stream>>>(s.evals.as<double>(), E, s.shift.as<double>(), m);
-        vec_resid_shift<T2>(c, B.X.template as<T2>(), B.Y.template as<T2>(), s.shift.as<double>(), m,
-                            s.resid.as<double>());
-        eps.resize(m);
-        res.resize(m);
-        FS_CUDA(cudaMemcpyAsync(eps.data(), s.evals.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        FS_CUDA(cudaMemcpyAsync(res.data(), s.resid.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        FS_CUDA(cudaStreamSynchronize(c->stream));
     }
 };
 
@@ -451,9 +527,10 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
     vec_damp_random(c, x0.as<double2>(), m, ncopy, c->opt.seed);
 
     int iters = 0, iters_mixed = 0;
-    double worst = 0;
     int status = 0;
     std::vector<double> eps, resid;
+    std::vector<int> order;
+    int nres = 0;
     Blocks<double2> B64;
     if (c->opt.precision == FS_MIXED) {
         ctx_ensure_fp32(c);
@@ -461,8 +538,11 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         B32.alloc(m, npw);
         vec_convert<double2, float2>(c, x0.as<double2>(), B32.X.as<float2>(), (size_t)m * npw);
         S.init_block<float2>(B32);
-        status = S.run<float2>(B32, c->opt.maxit, tol, true, iters, worst, 10);
+        status = S.run<float2>(B32, c->opt.maxit, tol, true, iters, 10, eps, resid, order, nres);
         iters_mixed = iters;
+        if (S.verbose)
+            fprintf(stderr, "[fs] FP32 stage: %d iterations, %.2f s, status %d\n", iters,
+                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), status);
         // carry the bands to FP64 (through x0, so that both block sets never coexist)
         vec_convert<float2, double2>(c, B32.X.as<float2>(), x0.as<double2>(), (size_t)m * npw);
         FS_CUDA(cudaStreamSynchronize(c->stream));
@@ -476,17 +556,33 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
                                 c->stream));
     }
     x0.release();
-    S.init_block<double2>(B64);
-    status = S.run<double2>(B64, std::max(0, c->opt.maxit - iters), tol, false, iters, worst);
-    S.final_rr<double2>(B64, eps, resid);
-    // order by (|eps - E|, eps)
-    std::vector<int> order(m);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        double da = std::fabs(eps[a] - e_ref), db = std::fabs(eps[b] - e_ref);
-        if (da != db) return da < db;
-        return eps[a] < eps[b];
-    });
+    bool done = false;
+    if (c->opt.precision == FS_MIXED && status == 1) {
+        // FP64 check of the FP32 result: Y = (H-E)X in FP64 for the wanted
+        // block only, Rayleigh-Ritz on H, FP64 residuals
+        std::vector<double> th(m);
+        FS_CUDA(cudaMemcpyAsync(th.data(), S.s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        int nw = nstates;
+        while (nw < m && th[nw] <= th[nstates - 1] * (1.0 + 1e-3)) ++nw;
+        S.HE(B64.X.as<double2>(), B64.Y.as<double2>(), nw);
+        S.h_ritz<double2>(B64, th, nres, eps, resid, order);
+        done = true;
+        for (int i : order) done = done && resid[i] <= tol;
+    }
+    if (!done) {
+        S.init_block<double2>(B64);
+        status = S.run<double2>(B64, std::max(0, c->opt.maxit - iters), tol, false, iters, 0, eps, resid, order, nres);
+    }
+    if (status != 1) {
+        // not converged: report the current H-Ritz pairs of the wanted block
+        std::vector<double> ra, th;
+        S.a_residuals(B64, ra, th);
+        S.h_ritz<double2>(B64, th, nres, eps, resid, order);
+    }
+    if (S.verbose)
+        fprintf(stderr, "[fs] done: %d iterations, %.2f s\n", iters,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
     c->result_states.ensure((size_t)nstates * npw * sizeof(double2));
     int nconv = 0;
     for (int i = 0; i < nstates; ++i) {
@@ -494,7 +590,7 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         res->eps[i] = eps[j];
         res->resid[i] = resid[j];
         if (resid[j] <= tol) ++nconv;
-        FS_CUDA(cudaMemcpyAsync(c->result_states.as<double2>() + (size_t)i * npw, B64.X.as<double2>() + (size_t)j * npw,
+        FS_CUDA(cudaMemcpyAsync(c->result_states.as<double2>() + (size_t)i * npw, B64.tX.as<double2>() + (size_t)j * npw,
                                 npw * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
     }
     FS_CUDA(cudaStreamSynchronize(c->stream));

@@ -15,9 +15,10 @@
 //     UMMA A = rows j' = 2g + c of the 2x2 real blocks [[re, -im], [im, re]]
 //     of B[k][g]; UMMA B = rows i of A(i,k) as (re, im) pairs; D[j'][i] is
 //     component c of C[i][g].
-// Operands are staged by the thread block (global -> registers -> split ->
-// shared memory in the canonical K-major no-swizzle layout), double
-// buffered; one thread issues the MMAs and commits them to an mbarrier.
+// Operands are staged by the thread block: global loads run two k-blocks
+// ahead into registers, then each value is split and stored to shared memory
+// in the canonical K-major no-swizzle layout (two stages); one thread issues
+// the MMAs of a stage and commits them to that stage's mbarrier.
 // Every mbarrier wait is bounded; on expiry the kernel raises the context's
 // error flag and stops issuing work.
 #include "fs_common.cuh"
@@ -29,7 +30,7 @@ namespace {
 constexpr int BK = 32;            // FP32 k elements per stage (128 bytes per row)
 constexpr int TM = 128;           // UMMA M (rows of the accumulator = TMEM lanes)
 constexpr int TN_MAX = 256;       // UMMA N maximum
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;
 constexpr int A_BYTES = TM * BK * 4;          // one split of the A tile
 constexpr int B_BYTES = TN_MAX * BK * 4;      // one split of the B tile
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
@@ -118,10 +119,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared machinery: TMEM allocation, the double-buffered k loop and the drain.
-// Producer(stage_base_hiA, loA, hiB, loB, kb) fills one stage.
+// Shared machinery: TMEM allocation, the k loop and the drain.
 struct TcCtl {
-    uint64_t* bar;       // [2]
+    uint64_t* bar;       // [2] one per stage: MMAs reading the stage have completed
     uint32_t* tslot;     // TMEM address written by tcgen05.alloc
     unsigned char* st[2];
 };
@@ -171,30 +171,150 @@ __device__ __forceinline__ void tc_issue(const TcCtl& t, int s, uint32_t tmem, u
     mma_commit(&t.bar[s]);
 }
 
-template <typename Producer>
-__device__ __forceinline__ bool tc_mainloop(const TcCtl& t, int nkb, uint32_t tmem, uint32_t idesc, Producer prod) {
-    bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb & 1;
-        if (kb >= 2) ok = ok && mbar_wait(&t.bar[s], ((kb - 2) >> 1) & 1);
-        if (!__syncthreads_and(ok)) {
-            // give the MMAs already issued one more bounded chance to finish
-            // before the caller releases tensor memory
-            mbar_wait(&t.bar[(kb - 1) & 1], ((kb - 1) >> 1) & 1);
-            return false;
+// split a 16-byte chunk into hi/lo and store both at byte offset off of (hi, lo)
+__device__ __forceinline__ void put4(unsigned char* hi, unsigned char* lo, uint32_t off, float4 v) {
+    float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+    float4 l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = l;
+}
+
+// two consecutive complex values of a row (zeros past kend); rows are only 8-byte aligned
+__device__ __forceinline__ float4 load2c(const float2* row, int k, int kend) {
+    float2 a = make_float2(0.f, 0.f), b = a;
+    if (k < kend) a = __ldg(row + k);
+    if (k + 1 < kend) b = __ldg(row + k + 1);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// The accumulation inside tensor memory loses accuracy with the length of
+// the chain (measured: the error of an H application grows about linearly
+// with the number of k-blocks accumulated in place).  Every DRAIN k-blocks
+// the partial tile is read out and added to FP32 registers with ordinary
+// round-to-nearest adds, and the next MMA starts a fresh chain.
+constexpr int DRAIN = 8;
+
+// Per thread: TMEM lanes 32 (w & 3) .. +31, columns 128 (w >> 2) .. +127.
+struct Acc {
+    float v[4][32];
+};
+
+__device__ __forceinline__ void drain_add(uint32_t tmem, int ncols, Acc& a) {
+    const int w = threadIdx.x >> 5;
+    const int c_base = 128 * (w >> 2);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c0 = c_base + 32 * j;
+        if (c0 < ncols) {  // warp-uniform
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
+#pragma unroll
+            for (int q = 0; q < 32; ++q) a.v[j][q] += v[q];
         }
-        prod(t.st[s], t.st[s] + A_BYTES, t.st[s] + 2 * A_BYTES, t.st[s] + 2 * A_BYTES + B_BYTES, kb);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) tc_issue(t, s, tmem, idesc, kb == 0);
     }
-    if (nkb > 0) ok = mbar_wait(&t.bar[(nkb - 1) & 1], ((nkb - 1) >> 1) & 1);
+}
+
+// One k-block: wait for the stage, store the registers loaded earlier, start
+// the loads two k-blocks ahead, then issue the stage's MMAs.
+template <class P>
+__device__ __forceinline__ bool tc_step(const TcCtl& t, int kb, int nkb, uint32_t tmem, uint32_t idesc, P& p,
+                                        typename P::Regs& r) {
+    const int s = kb & 1;
+    bool ok = true;
+    if (kb >= 2) ok = mbar_wait(&t.bar[s], ((kb - 2) >> 1) & 1);
+    if (!__syncthreads_and(ok)) {
+        // give the MMAs already issued one more bounded chance to finish
+        // before the caller releases tensor memory
+        mbar_wait(&t.bar[(kb - 1) & 1], ((kb - 1) >> 1) & 1);
+        return false;
+    }
+    p.store(r, t.st[s], t.st[s] + A_BYTES, t.st[s] + 2 * A_BYTES, t.st[s] + 2 * A_BYTES + B_BYTES);
+    if (kb + 2 < nkb) p.load(r, kb + 2);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) tc_issue(t, s, tmem, idesc, kb % DRAIN == 0);
+    return true;
+}
+
+// Wait for the MMAs of k-block kb, add the tile to the registers, and make
+// sure every thread has read tensor memory before the next chain overwrites it.
+__device__ __forceinline__ bool tc_drain(const TcCtl& t, int kb, uint32_t tmem, int ncols, Acc& a) {
+    bool ok = mbar_wait(&t.bar[kb & 1], (kb >> 1) & 1);
+    if (!__syncthreads_and(ok)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return __syncthreads_and(ok);
+    drain_add(tmem, ncols, a);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    return true;
+}
+
+template <class P>
+__device__ bool tc_run(const TcCtl& t, int nkb, uint32_t tmem, uint32_t idesc, int ncols, P& p, Acc& a) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int q = 0; q < 32; ++q) a.v[j][q] = 0.f;
+    typename P::Regs r0, r1;
+    if (nkb > 0) p.load(r0, 0);
+    if (nkb > 1) p.load(r1, 1);
+    for (int kb = 0; kb < nkb; kb += 2) {
+        if (!tc_step(t, kb, nkb, tmem, idesc, p, r0)) return false;
+        if ((kb % DRAIN == DRAIN - 1 || kb == nkb - 1) && !tc_drain(t, kb, tmem, ncols, a)) return false;
+        if (kb + 1 < nkb) {
+            if (!tc_step(t, kb + 1, nkb, tmem, idesc, p, r1)) return false;
+            if (((kb + 1) % DRAIN == DRAIN - 1 || kb + 1 == nkb - 1) && !tc_drain(t, kb + 1, tmem, ncols, a))
+                return false;
+        }
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------- Gram form
 // part[z][i][j] (float2) = sum over this split's k of conj(A[i][k]) B[j][k]
+struct GramP {
+    const float2* A;
+    long lda;
+    const int* amap;
+    const float2* B;
+    long ldb;
+    const int* bmap;
+    int M, N, i0, j0, nj, kbeg, kend;
+    struct Regs {
+        float4 a[4], b[4];
+    };
+    // A task t in [0, 1024): row (t>>6)*8 + (t&7), chunk (t>>3)&7 -> smem byte 16 t
+    // B task t in [0, 1024): source row (t>>5)*4 + (t&3), chunk (t>>2)&7
+    __device__ __forceinline__ void load(Regs& r, int kb) const {
+        const int kc0 = kbeg + kb * (BK / 2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = threadIdx.x + THREADS * q;
+            const int row = ((t >> 6) << 3) + (t & 7), ch = (t >> 3) & 7;
+            const int i = i0 + row;
+            r.a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < M) r.a[q] = load2c(A + (amap ? (long)amap[i] : (long)i) * lda, kc0 + 2 * ch, kend);
+            const int jj = ((t >> 5) << 2) + (t & 3), chb = (t >> 2) & 7;
+            r.b[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (jj < nj) {
+                const int j = j0 + jj;
+                r.b[q] = load2c(B + (bmap ? (long)bmap[j] : (long)j) * ldb, kc0 + 2 * chb, kend);
+            }
+        }
+    }
+    __device__ __forceinline__ void store(const Regs& r, unsigned char* ahi, unsigned char* alo, unsigned char* bhi,
+                                          unsigned char* blo) const {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = threadIdx.x + THREADS * q;
+            put4(ahi, alo, 16u * t, r.a[q]);
+            const int jj = ((t >> 5) << 2) + (t & 3), chb = (t >> 2) & 7;
+            const float4 v = r.b[q];
+            put4(bhi, blo, kmaj(2 * jj, 4 * chb), v);
+            put4(bhi, blo, kmaj(2 * jj + 1, 4 * chb), make_float4(v.y, -v.x, v.w, -v.z));
+        }
+    }
+};
+
 __global__ void __launch_bounds__(THREADS)
 tc_gram_kernel(int M, int N, int K, const float2* __restrict__ A, long lda, const int* __restrict__ amap,
                const float2* __restrict__ B, long ldb, const int* __restrict__ bmap, float2* __restrict__ part,
@@ -202,61 +322,36 @@ tc_gram_kernel(int M, int N, int K, const float2* __restrict__ A, long lda, cons
     extern __shared__ __align__(1024) unsigned char smem[];
     TcCtl t = tc_setup(smem);
     const uint32_t tmem = *t.tslot;
-    const int i0 = blockIdx.x * TM;
-    const int j0 = blockIdx.y * (TN_MAX / 2);
-    const int nj = min(TN_MAX / 2, N - j0);
-    const int ncols = ((2 * nj + 15) / 16) * 16;  // UMMA N
-    const int kbeg = blockIdx.z * kchunk;          // complex k
-    const int kend = min(K, kbeg + kchunk);
-    const int nkb = (2 * (kend - kbeg) + BK - 1) / BK;
-    const uint32_t idesc = idesc_tf32(TM, ncols);
-    auto prod = [&](unsigned char* ahi, unsigned char* alo, unsigned char* bhi, unsigned char* blo, int kb) {
-        const int kc0 = kbeg + kb * (BK / 2);  // first complex k of the stage
-        // A: 128 rows x 8 chunks of 2 complex
-        for (int task = threadIdx.x; task < TM * (BK / 4); task += THREADS) {
-            int r = task >> 3, ch = task & 7;
-            int i = i0 + r, k = kc0 + 2 * ch;
-            float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-            if (i < M) {
-                const float2* row = A + (amap ? (long)amap[i] : (long)i) * lda;
-                if (k < kend) v0 = row[k];
-                if (k + 1 < kend) v1 = row[k + 1];
-            }
-            uint32_t o = kmaj(r, 4 * ch);
-            put2(ahi, alo, o, v0.x, v0.y);
-            put2(ahi, alo, o + 8, v1.x, v1.y);
-        }
-        // B: rows 2j (b) and 2j+1 (rotated), zero beyond nj up to ncols
-        for (int task = threadIdx.x; task < (ncols / 2) * (BK / 4); task += THREADS) {
-            int jj = task >> 3, ch = task & 7;
-            int j = j0 + jj, k = kc0 + 2 * ch;
-            float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-            if (jj < nj) {
-                const float2* row = B + (bmap ? (long)bmap[j] : (long)j) * ldb;
-                if (k < kend) v0 = row[k];
-                if (k + 1 < kend) v1 = row[k + 1];
-            }
-            uint32_t o0 = kmaj(2 * jj, 4 * ch), o1 = kmaj(2 * jj + 1, 4 * ch);
-            put2(bhi, blo, o0, v0.x, v0.y);
-            put2(bhi, blo, o0 + 8, v1.x, v1.y);
-            put2(bhi, blo, o1, v0.y, -v0.x);
-            put2(bhi, blo, o1 + 8, v1.y, -v1.x);
-        }
-    };
-    bool ok = tc_mainloop(t, nkb, tmem, idesc, prod);
+    GramP p;
+    p.A = A;
+    p.lda = lda;
+    p.amap = amap;
+    p.B = B;
+    p.ldb = ldb;
+    p.bmap = bmap;
+    p.M = M;
+    p.N = N;
+    p.i0 = blockIdx.x * TM;
+    p.j0 = blockIdx.y * (TN_MAX / 2);
+    p.nj = min(TN_MAX / 2, N - p.j0);
+    p.kbeg = blockIdx.z * kchunk;
+    p.kend = min(K, p.kbeg + kchunk);
+    const int ncols = ((2 * p.nj + 15) / 16) * 16;  // UMMA N
+    const int nkb = (2 * (p.kend - p.kbeg) + BK - 1) / BK;
+    Acc acc;
+    bool ok = tc_run(t, nkb, tmem, idesc_tf32(TM, ncols), ncols, p, acc);
     if (ok) {
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int r = 32 * w + lane;
-        const int i = i0 + r;
-        float2* out = part + ((long)blockIdx.z * M + i) * N + j0;
-        for (int c0 = 0; c0 < ncols; c0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + c0, v);
-            if (i < M) {
+        const int i = p.i0 + 32 * (w & 3) + lane;
+        float2* out = part + ((long)blockIdx.z * M + i) * N + p.j0;
+        if (i < M) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c0 = 128 * (w >> 2) + 32 * j;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     int jj = c0 / 2 + q;
-                    if (jj < nj) out[jj] = make_float2(v[2 * q], v[2 * q + 1]);
+                    if (jj < p.nj) out[jj] = make_float2(acc.v[j][2 * q], acc.v[j][2 * q + 1]);
                 }
             }
         }
@@ -288,63 +383,98 @@ __global__ void tc_gram_reduce_kernel(int M, int N, int splits, const float2* __
 }
 
 // ---------------------------------------------------------------- apply form
-// C[ic(i)][g] = alpha sum_k A(i,k) B[ib(k)][g] + beta D[ic(i)][g]
-template <typename A2>
+// C[ic(i)][g] = alpha sum_k coef[i][k] B[ib(k)][g] + beta D[ic(i)][g], coef compact [M][K] float2
+struct NnP {
+    const float2* B;
+    long ldb;
+    const int* bmap;
+    const float2* coef;
+    int ldk;
+    int N, K, g0, i0, ni, ncols;
+    struct Regs {
+        float4 v[2], c[8];
+    };
+    // UMMA A task t in [0, 512): plane wave g0 + (t & 63), complex k pair t >> 6
+    // UMMA B task t in [0, 2048): coefficient row (t>>6)*8 + (t&7), chunk (t>>3)&7 -> smem byte 16 t
+    __device__ __forceinline__ void load(Regs& r, int kb) const {
+        const int kc0 = kb * (BK / 2);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int t = threadIdx.x + THREADS * q;
+            const int g = g0 + (t & 63), k = kc0 + 2 * (t >> 6);
+            float2 a = make_float2(0.f, 0.f), b = a;
+            if (g < N) {
+                if (k < K) a = __ldg(B + (bmap ? (long)bmap[k] : (long)k) * ldb + g);
+                if (k + 1 < K) b = __ldg(B + (bmap ? (long)bmap[k + 1] : (long)(k + 1)) * ldb + g);
+            }
+            r.v[q] = make_float4(a.x, a.y, b.x, b.y);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int t = threadIdx.x + THREADS * q;
+            const int row = ((t >> 6) << 3) + (t & 7), ch = (t >> 3) & 7;
+            r.c[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (row < ni) r.c[q] = load2c(coef + (long)(i0 + row) * ldk, kc0 + 2 * ch, K);
+        }
+    }
+    __device__ __forceinline__ void store(const Regs& r, unsigned char* ahi, unsigned char* alo, unsigned char* bhi,
+                                          unsigned char* blo) const {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int t = threadIdx.x + THREADS * q;
+            const int gg = t & 63, kp = t >> 6;
+            const float4 v = r.v[q];  // (re_k, im_k, re_k+1, im_k+1)
+            put4(ahi, alo, kmaj(2 * gg, 4 * kp), make_float4(v.x, -v.y, v.z, -v.w));
+            put4(ahi, alo, kmaj(2 * gg + 1, 4 * kp), make_float4(v.y, v.x, v.w, v.z));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int t = threadIdx.x + THREADS * q;
+            const int row = ((t >> 6) << 3) + (t & 7);
+            if (row < ncols) put4(bhi, blo, 16u * t, r.c[q]);
+        }
+    }
+};
+
 __global__ void __launch_bounds__(THREADS)
-tc_nn_kernel(int M, int N, int K, const A2* __restrict__ A, long ai, long ak, const float2* __restrict__ B, long ldb,
+tc_nn_kernel(int M, int N, int K, const float2* __restrict__ coef, int ldk, const float2* __restrict__ B, long ldb,
              const int* __restrict__ bmap, float2* C, long ldc, const int* __restrict__ cmap, float alpha, float beta,
              const float2* D, long ldd, int* errflag) {
     extern __shared__ __align__(1024) unsigned char smem[];
     TcCtl t = tc_setup(smem);
     const uint32_t tmem = *t.tslot;
-    const int g0 = blockIdx.x * (TM / 2);     // 64 plane waves per tile
-    const int i0 = blockIdx.y * TN_MAX;
-    const int ni = min(TN_MAX, M - i0);
-    const int ncols = ((ni + 15) / 16) * 16;
+    NnP p;
+    p.B = B;
+    p.ldb = ldb;
+    p.bmap = bmap;
+    p.coef = coef;
+    p.ldk = ldk;
+    p.N = N;
+    p.K = K;
+    p.g0 = blockIdx.x * (TM / 2);
+    p.i0 = blockIdx.y * TN_MAX;
+    p.ni = min(TN_MAX, M - p.i0);
+    p.ncols = ((p.ni + 15) / 16) * 16;
     const int nkb = (2 * K + BK - 1) / BK;
-    const uint32_t idesc = idesc_tf32(TM, ncols);
-    auto prod = [&](unsigned char* ahi, unsigned char* alo, unsigned char* bhi, unsigned char* blo, int kb) {
-        const int kc0 = kb * (BK / 2);
-        // UMMA A: 64 plane waves x 16 complex k -> rows 2g+c, k' = 2k+c'
-        for (int task = threadIdx.x; task < (TM / 2) * (BK / 2); task += THREADS) {
-            int gg = task & 63, kk = task >> 6;
-            int g = g0 + gg, k = kc0 + kk;
-            float2 v = make_float2(0.f, 0.f);
-            if (g < N && k < K) v = B[(bmap ? (long)bmap[k] : (long)k) * ldb + g];
-            put2(ahi, alo, kmaj(2 * gg, 2 * kk), v.x, -v.y);
-            put2(ahi, alo, kmaj(2 * gg + 1, 2 * kk), v.y, v.x);
-        }
-        // UMMA B: coefficient rows i, (re, im) pairs
-        for (int task = threadIdx.x; task < ncols * (BK / 2); task += THREADS) {
-            int ii = task / (BK / 2), kk = task % (BK / 2);
-            int i = i0 + ii, k = kc0 + kk;
-            float re = 0.f, im = 0.f;
-            if (ii < ni && k < K) {
-                A2 a = A[(long)i * ai + (long)k * ak];
-                re = (float)a.x;
-                im = (float)a.y;
-            }
-            put2(bhi, blo, kmaj(ii, 2 * kk), re, im);
-        }
-    };
-    bool ok = tc_mainloop(t, nkb, tmem, idesc, prod);
+    Acc acc;
+    bool ok = tc_run(t, nkb, tmem, idesc_tf32(TM, p.ncols), p.ncols, p, acc);
     if (ok) {
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int r = 32 * w + lane;          // j' = 2g + c
-        const int g = g0 + (r >> 1);
+        const int r = 32 * (w & 3) + lane;  // j' = 2g + c
+        const int g = p.g0 + (r >> 1);
         const int comp = r & 1;
         float* Cf = reinterpret_cast<float*>(C);
         const float* Df = reinterpret_cast<const float*>(D);
-        for (int c0 = 0; c0 < ncols; c0 += 32) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + c0, v);
-            if (g < N) {
+        if (g < N) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c0 = 128 * (w >> 2) + 32 * j;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     int ii = c0 + q;
-                    if (ii < ni) {
-                        long row = cmap ? (long)cmap[i0 + ii] : (long)(i0 + ii);
-                        float o = alpha * v[q];
+                    if (ii < p.ni) {
+                        long row = cmap ? (long)cmap[p.i0 + ii] : (long)(p.i0 + ii);
+                        float o = alpha * acc.v[j][q];
                         if (beta != 0.f) o += beta * Df[(row * ldd + g) * 2 + comp];
                         Cf[(row * ldc + g) * 2 + comp] = o;
                     }
@@ -357,18 +487,26 @@ tc_nn_kernel(int M, int N, int K, const A2* __restrict__ A, long ai, long ak, co
     tc_teardown(t);
 }
 
+// coef[i][k] = A(i, k) as float2, compact
+template <typename A2>
+__global__ void pack_coef_kernel(const A2* __restrict__ A, long ai, long ak, int M, int K, float2* __restrict__ coef) {
+    long total = (long)M * K;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        long i = t / K, k = t - i * K;
+        A2 a = A[i * ai + k * ak];
+        coef[t] = make_float2((float)a.x, (float)a.y);
+    }
+}
+
 bool g_attr_set = false;
 void set_attrs() {
     if (g_attr_set) return;
     cudaFuncSetAttribute((const void*)tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute((const void*)tc_nn_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute((const void*)tc_nn_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute((const void*)tc_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     g_attr_set = true;
 }
 
 }  // namespace
-
-int* ctx_errflag(fs_ctx* c);
 
 void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, const int* amap, const float2* B,
                   long ldb, const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid) {
@@ -376,10 +514,11 @@ void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, con
     set_attrs();
     ProfScope ps(c, kid, ((double)M + N) * K * sizeof(float2) + (double)M * N * sizeof(double2), 8.0 * M * N * K);
     int tm = (M + TM - 1) / TM, tn = (N + TN_MAX / 2 - 1) / (TN_MAX / 2);
-    int want = std::max(1, (2 * 152 + tm * tn - 1) / (tm * tn));
+    int want = std::max(1, (2 * 148 + tm * tn - 1) / (tm * tn));
     int maxs = std::max(1, K / 1024);
     int splits = std::min(want, maxs);
     int kchunk = (K + splits - 1) / splits;
+    kchunk = std::min(kchunk, c->tc_gram_kchunk);
     kchunk = ((kchunk + BK / 2 - 1) / (BK / 2)) * (BK / 2);
     splits = std::max(1, (K + kchunk - 1) / kchunk);
     c->splitk.ensure((size_t)splits * M * N * sizeof(float2));
@@ -400,10 +539,24 @@ void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, c
     set_attrs();
     ProfScope ps(c, kid, ((double)K + M * (beta != 0.0 ? 2.0 : 1.0)) * N * sizeof(float2) + (double)M * K * sizeof(A2),
                  8.0 * M * N * K);
+    c->coefbuf.ensure((size_t)M * K * sizeof(float2));
+    long total = (long)M * K;
+    pack_coef_kernel<A2><<<(int)std::min<long>(1024, (total + 255) / 256), 256, 0, c->stream>>>(
+        A, ai, ak, M, K, c->coefbuf.as<float2>());
     dim3 g((N + TM / 2 - 1) / (TM / 2), (M + TN_MAX - 1) / TN_MAX);
-    tc_nn_kernel<A2><<<g, THREADS, SMEM_BYTES, c->stream>>>(M, N, K, A, ai, ak, B, ldb, bmap, C, ldc, cmap,
-                                                            (float)alpha, (float)beta, D, ldd, ctx_errflag(c));
-    FS_CUDA(cudaGetLastError());
+    // the tensor-memory accumulation runs over at most tc_nn_kchunk complex k
+    // per launch; longer sums continue in FP32 global memory (beta = 1)
+    const int kc = std::max(BK / 2, c->tc_nn_kchunk);
+    for (int k0 = 0; k0 < K; k0 += kc) {
+        const int kk = std::min(kc, K - k0);
+        const bool first = k0 == 0;
+        const int* bm = bmap ? bmap + k0 : nullptr;
+        const float2* Bk = bmap ? B : B + (long)k0 * ldb;
+        tc_nn_kernel<<<g, THREADS, SMEM_BYTES, c->stream>>>(
+            M, N, kk, c->coefbuf.as<float2>() + k0, K, Bk, ldb, bm, C, ldc, cmap, (float)alpha,
+            first ? (float)beta : 1.0f, first ? D : C, first ? ldd : ldc, ctx_errflag(c));
+        FS_CUDA(cudaGetLastError());
+    }
 }
 
 template void tc_gemm_nn<double2>(fs_ctx*, int, int, int, const double2*, long, long, const float2*, long, const int*,

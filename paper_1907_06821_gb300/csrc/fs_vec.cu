@@ -107,18 +107,16 @@ __global__ void scale_rows_kernel(T2* X, const int* __restrict__ map, long npw, 
         x[g] = cscale(x[g], inv);
 }
 
-// W[a] = M_i(q) (Z[i] - theta_i X[i]),  i = act[a]
+// W[a] = M_i(q) R[act[a]]
 //   precond 0: paper's M(q) = 1 / ((|q|^2/2 - E)^2 + dE^2)
 //   precond 1: folded Teter-Payne-Allan form K(x)^2 / T_i^2 with x = (|q|^2/2) / T_i
 template <typename T2>
-__global__ void make_w_kernel(const T2* __restrict__ X, const T2* __restrict__ Z, const double* __restrict__ theta,
-                              const int* __restrict__ act, long npw, T2* __restrict__ W, const double* __restrict__ kin,
-                              double e_ref, double dE2, int precond, const double* __restrict__ band_kin) {
-    using R = typename real_of<T2>::t;
+__global__ void make_w_kernel(const T2* __restrict__ R, const int* __restrict__ act, long npw, T2* __restrict__ W,
+                              const double* __restrict__ kin, double e_ref, double dE2, int precond,
+                              const double* __restrict__ band_kin) {
+    using Rl = typename real_of<T2>::t;
     const int i = act[blockIdx.y];
-    const R th = (R)theta[i];
-    const T2* x = X + (long)i * npw;
-    const T2* z = Z + (long)i * npw;
+    const T2* r = R + (long)i * npw;
     T2* w = W + (long)blockIdx.y * npw;
     double tk = band_kin ? fmax(band_kin[i], 1e-3) : 1.0;
     for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < npw; g += (long)gridDim.x * blockDim.x) {
@@ -132,9 +130,53 @@ __global__ void make_w_kernel(const T2* __restrict__ X, const T2* __restrict__ Z
             double d = kin[g] - e_ref;
             m = 1.0 / (d * d + dE2);
         }
-        T2 a = x[g], b = z[g];
-        w[g] = mk((R)m * (b.x - th * a.x), (R)m * (b.y - th * a.y));
+        T2 a = r[g];
+        w[g] = mk((Rl)m * a.x, (Rl)m * a.y);
     }
+}
+
+// RH[i] = y_i - d_i x_i with d_i = <x_i, y_i>  (the H residual of band i)
+template <typename T2>
+__global__ void rh_kernel(const T2* __restrict__ X, const T2* __restrict__ Y, const double2* __restrict__ dots,
+                          long npw, T2* __restrict__ RH) {
+    using Rl = typename real_of<T2>::t;
+    const long i = blockIdx.y;
+    const double2 d = dots[i];
+    const T2* x = X + i * npw;
+    const T2* y = Y + i * npw;
+    T2* o = RH + i * npw;
+    for (long g = blockIdx.x * (long)blockDim.x + threadIdx.x; g < npw; g += (long)gridDim.x * blockDim.x) {
+        T2 a = x[g], b = y[g];
+        o[g] = mk((Rl)(b.x - (d.x * a.x - d.y * a.y)), (Rl)(b.y - (d.x * a.y + d.y * a.x)));
+    }
+}
+
+// A residual from the H residual r = y - d x:  (H-E)^2 x - theta x
+//   = (H-E) r + d r + (d^2 - theta) x,   written over RH;  ra_i = its norm.
+// Every term is computed from the small vector r, so its rounding error
+// scales with ||r|| instead of with ||(H-E) y||.
+template <typename T2>
+__global__ void __launch_bounds__(RT) a_resid_kernel(const T2* __restrict__ ZR, T2* RH, const T2* __restrict__ X,
+                                                     const double2* __restrict__ dots,
+                                                     const double* __restrict__ theta, long npw, double* ra) {
+    using Rl = typename real_of<T2>::t;
+    __shared__ double sh[33];
+    const long i = blockIdx.x;
+    const double2 d = dots[i];
+    const double c0x = d.x * d.x - d.y * d.y - theta[i], c0y = 2.0 * d.x * d.y;
+    const T2* z = ZR + i * npw;
+    const T2* x = X + i * npw;
+    T2* r = RH + i * npw;
+    double s = 0;
+    for (long g = threadIdx.x; g < npw; g += blockDim.x) {
+        T2 a = z[g], b = r[g], c = x[g];
+        double ox = (double)a.x + (d.x * b.x - d.y * b.y) + (c0x * c.x - c0y * c.y);
+        double oy = (double)a.y + (d.x * b.y + d.y * b.x) + (c0x * c.y + c0y * c.x);
+        r[g] = mk((Rl)ox, (Rl)oy);
+        s += ox * ox + oy * oy;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) ra[i] = sqrt(s);
 }
 
 // splitmix64 (Steele, Lea and Flood 2014) as a counter-based generator
@@ -196,13 +238,30 @@ void vec_resid_shift(fs_ctx* c, const T2* X, const T2* Y, const double* shift, i
 }
 
 template <typename T2>
-void vec_make_w(fs_ctx* c, const T2* X, const T2* Z, const double* theta, const int* act, int na, T2* W, double e_ref,
-                double dE, int precond, const double* band_kin) {
+void vec_make_w(fs_ctx* c, const T2* R, const int* act, int na, T2* W, double e_ref, double dE, int precond,
+                const double* band_kin) {
     if (na <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 3.0 * na * c->npw * sizeof(T2) + c->npw * 8.0, 8.0 * na * c->npw);
+    ProfScope ps(c, KS_VECTOR, 2.0 * na * c->npw * sizeof(T2) + c->npw * 8.0, 6.0 * na * c->npw);
     dim3 g(gx_for(c->npw), na);
-    make_w_kernel<T2><<<g, 256, 0, c->stream>>>(X, Z, theta, act, c->npw, W, c->kin.as<double>(), e_ref, dE * dE,
-                                                 precond, band_kin);
+    make_w_kernel<T2><<<g, 256, 0, c->stream>>>(R, act, c->npw, W, c->kin.as<double>(), e_ref, dE * dE, precond,
+                                                 band_kin);
+    FS_CUDA(cudaGetLastError());
+}
+
+template <typename T2> void vec_rh(fs_ctx* c, const T2* X, const T2* Y, const double2* dots, int m, T2* RH) {
+    if (m <= 0) return;
+    ProfScope ps(c, KS_VECTOR, 3.0 * m * c->npw * sizeof(T2), 8.0 * m * c->npw);
+    dim3 g(gx_for(c->npw), m);
+    rh_kernel<T2><<<g, 256, 0, c->stream>>>(X, Y, dots, c->npw, RH);
+    FS_CUDA(cudaGetLastError());
+}
+
+template <typename T2>
+void vec_a_resid(fs_ctx* c, const T2* ZR, T2* RH, const T2* X, const double2* dots, const double* theta, int m,
+                 double* ra) {
+    if (m <= 0) return;
+    ProfScope ps(c, KS_VECTOR, 4.0 * m * c->npw * sizeof(T2), 20.0 * m * c->npw);
+    a_resid_kernel<T2><<<m, RT, 0, c->stream>>>(ZR, RH, X, dots, theta, c->npw, ra);
     FS_CUDA(cudaGetLastError());
 }
 
@@ -245,8 +304,10 @@ template <typename S2, typename T2> void vec_convert(fs_ctx* c, const S2* in, T2
 #define INST(T2)                                                                                           \
     template void vec_resid<T2>(fs_ctx*, const T2*, const T2*, int, double*, double2*);                     \
     template void vec_resid_shift<T2>(fs_ctx*, const T2*, const T2*, const double*, int, double*);          \
-    template void vec_make_w<T2>(fs_ctx*, const T2*, const T2*, const double*, const int*, int, T2*, double, \
-                                 double, int, const double*);                                               \
+    template void vec_make_w<T2>(fs_ctx*, const T2*, const int*, int, T2*, double, double, int, const double*); \
+    template void vec_rh<T2>(fs_ctx*, const T2*, const T2*, const double2*, int, T2*);                      \
+    template void vec_a_resid<T2>(fs_ctx*, const T2*, T2*, const T2*, const double2*, const double*, int,   \
+                                  double*);                                                                 \
     template void vec_row_norms<T2>(fs_ctx*, const T2*, const int*, int, double*);                          \
     template void vec_scale_rows<T2>(fs_ctx*, T2*, const int*, int, const double*);
 INST(double2)

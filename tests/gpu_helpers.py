@@ -29,3 +29,13 @@ CASES = {
 
 def oracle_ham(w):
     return pw.Hamiltonian(w)
+
+
+def dense_box():
+    """18 wells, 2,309 plane waves, 40 states in the middle of a dense spectrum
+    (level spacing ~3e-3 Ha, near-mirror pairs about E)."""
+    w = fi.make_box(L=(16., 16., 24.), n=(24, 24, 36), ecut=4.0, natom=18, widths=(1.0,), nstates=40,
+                    e_ref=None, seed=7)
+    e = np.linalg.eigvalsh(pw.dense_H(w))
+    w.e_ref = 0.5 * (e[60] + e[61])
+    return w

@@ -11,7 +11,7 @@ import pytest
 
 import fs_inputs as fi
 from oracle import planewave as pw
-from gpu_helpers import CASES, rel_err, small_box
+from gpu_helpers import CASES, dense_box, rel_err, small_box
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -113,9 +113,9 @@ def _check_solution(w, r, states, eb):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("case", ["tiny", "box_radix5_two_widths", "box_k_radix35"])
+@pytest.mark.parametrize("case", ["tiny", "box_radix5_two_widths", "box_k_radix35", "box_dense"])
 def test_solve_matches_lapack(fs, case, precision):
-    w = CASES[case]()
+    w = CASES[case]() if case in CASES else dense_box()
     eb, _, _ = pw.brute_nearest(w, w.e_ref, w.nstates)
     prec = fs.FS_FP64 if precision == "fp64" else fs.FS_MIXED
     with make_ctx(fs, w, precision=prec) as c:
