@@ -107,6 +107,23 @@ __global__ void row_scale_kernel(double2* C, int n, int m, const double* d) {
 }
 
 inline int nblk(long total) { return (int)((total + 255) / 256); }
+
+// smallest squared diagonal entry of the Cholesky factor left in L (n x n)
+__global__ void min_pivot_kernel(const double2* L, int n, double* out) {
+    __shared__ double sh[256];
+    double v = 1e300;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double d = L[(long)i * n + i].x;
+        v = fmin(v, d * d);
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmin(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
 inline int nblk_(long total) { return nblk(total); }
 
 // G(i, j) = conj(G(j, i)) where the block of i (boundaries b1 <= b2) is below the block of j
@@ -192,12 +209,35 @@ struct Solver {
     // directions whose eigenvalue is below tau * max (near-dependent vectors
     // in FP32), instead of a Cholesky factorisation of GB.  Returns the
     // cuSOLVER info (0 = success).
-    int rr_basis(int nb, bool robust, double tau) {
+    int rr_basis(int nb, bool robust, double tau, double piv_floor) {
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
         if (!robust) return hegvd(nb);
         diag_invsqrt_kernel<<<nblk(nb), 256, 0, c->stream>>>(GB, nb, s.dscale.as<double>());
         sym_scale_kernel<<<nblk((long)nb * nb), 256, 0, c->stream>>>(GA, GB, nb, s.dscale.as<double>());
+        {
+            // fast path: Cholesky-based generalized eigensolve of the scaled
+            // problem, accepted when every Cholesky pivot of the unit-diagonal
+            // G_B is above tau (no near-dependent direction)
+            const size_t bytes = (size_t)nb * nb * sizeof(double2);
+            FS_CUDA(cudaMemcpyAsync(s.T1.p, GA, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            FS_CUDA(cudaMemcpyAsync(s.T2.p, GB, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            int info = hegvd(nb);
+            if (info == 0) {
+                min_pivot_kernel<<<1, 256, 0, c->stream>>>(GB, nb, s.nrm.as<double>());
+                double piv = 0;
+                FS_CUDA(cudaMemcpyAsync(&piv, s.nrm.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                FS_CUDA(cudaStreamSynchronize(c->stream));
+                if (piv > piv_floor) {
+                    row_scale_kernel<<<nblk((long)nb * m), 256, 0, c->stream>>>(GA, nb, m, s.dscale.as<double>());
+                    FS_CUDA(cudaGetLastError());
+                    last_kept = nb;
+                    return 0;
+                }
+            }
+            FS_CUDA(cudaMemcpyAsync(GA, s.T1.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            FS_CUDA(cudaMemcpyAsync(GB, s.T2.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        }
         int info = heevd(nb, GB);
         if (info != 0) return info;
         std::vector<double> lam(nb);
@@ -235,6 +275,8 @@ struct Solver {
 
     template <typename T2> static constexpr bool is_fp32() { return sizeof(T2) == 8; }
     template <typename T2> static double tau_for() { return sizeof(T2) == 8 ? 1e-6 : 1e-11; }
+    // pivot floor of the Cholesky fast path (the scaled G_B has unit diagonal)
+    template <typename T2> static double piv_for() { return sizeof(T2) == 8 ? 1e-3 : 1e-8; }
 
     // Hermitian Gram matrix of the basis blocks into G (nb x nb column-major):
     // G(i, j) = <S_i, T_j> computed for row block >= column block (T = S or
@@ -261,7 +303,7 @@ struct Solver {
         double2* GB = s.GB.as<double2>();
         gemm_gram<T2>(c, m, m, c->npw, Y, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
         gemm_gram<T2>(c, m, m, c->npw, X, c->npw, nullptr, X, c->npw, nullptr, GB, 1, m, 1.0, 0.0);
-        int info = rr_basis(m, true, tau_for<T2>());
+        int info = rr_basis(m, true, tau_for<T2>(), piv_for<T2>());
         if (info != 0) throw fs_error(FS_ERR_NUMERIC, "start block is rank deficient (info " + std::to_string(info) + ")");
         rotate_simple(B, m);
         FS_CUDA(cudaMemcpyAsync(s.theta.p, s.evals.p, m * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -402,7 +444,7 @@ struct Solver {
             // Rayleigh quotients of A accurate in the FP32 stage
             gram_blocks<T2>(GA, nb, SY, SY, maps, sizes, offs, nblk);
             gram_blocks<T2>(GB, nb, S, S, maps, sizes, offs, nblk);
-            int info = rr_basis(nb, true, tau_for<T2>());
+            int info = rr_basis(nb, true, tau_for<T2>(), piv_for<T2>());
             if (info != 0) {
                 if (useP) {
                     useP = false;
@@ -532,43 +574,44 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
     std::vector<int> order;
     int nres = 0;
     Blocks<double2> B64;
+    bool done = false;
     if (c->opt.precision == FS_MIXED) {
         ctx_ensure_fp32(c);
         Blocks<float2> B32;
         B32.alloc(m, npw);
         vec_convert<double2, float2>(c, x0.as<double2>(), B32.X.as<float2>(), (size_t)m * npw);
+        x0.release();
         S.init_block<float2>(B32);
-        status = S.run<float2>(B32, c->opt.maxit, tol, true, iters, 10, eps, resid, order, nres);
-        iters_mixed = iters;
-        if (S.verbose)
-            fprintf(stderr, "[fs] FP32 stage: %d iterations, %.2f s, status %d\n", iters,
-                    std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), status);
-        // carry the bands to FP64 (through x0, so that both block sets never coexist)
-        vec_convert<float2, double2>(c, B32.X.as<float2>(), x0.as<double2>(), (size_t)m * npw);
-        FS_CUDA(cudaStreamSynchronize(c->stream));
-        B32.free_all();
         B64.alloc(m, npw);
-        FS_CUDA(cudaMemcpyAsync(B64.X.p, x0.p, (size_t)m * npw * sizeof(double2), cudaMemcpyDeviceToDevice,
-                                c->stream));
+        // FP32 stage to a margin below tol (its residuals carry FP32 noise), then
+        // an FP64 check of the wanted bands: Y = (H-E)X in FP64 for those bands
+        // only, Rayleigh-Ritz on H with the FP64 overlap, FP64 residuals.  A
+        // failed check tightens the FP32 target; a stalled FP32 stage hands over
+        // to FP64 iterations.
+        for (double margin : {0.5, 0.25, 0.125}) {
+            status = S.run<float2>(B32, c->opt.maxit - iters, margin * tol, true, iters, 10, eps, resid, order, nres);
+            if (S.verbose)
+                fprintf(stderr, "[fs] FP32 stage to %.2f tol: %d iterations, %.2f s, status %d\n", margin, iters,
+                        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), status);
+            vec_convert<float2, double2>(c, B32.X.as<float2>(), B64.X.as<double2>(), (size_t)m * npw);
+            if (status != 1) break;
+            std::vector<double> th(m);
+            FS_CUDA(cudaMemcpyAsync(th.data(), S.s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            FS_CUDA(cudaStreamSynchronize(c->stream));
+            int nw = nstates;
+            while (nw < m && th[nw] <= th[nstates - 1] * (1.0 + 1e-3)) ++nw;
+            S.HE(B64.X.as<double2>(), B64.Y.as<double2>(), nw);
+            S.h_ritz<double2>(B64, th, nres, eps, resid, order);
+            done = true;
+            for (int i : order) done = done && resid[i] <= tol;
+            if (done || iters >= c->opt.maxit) break;
+        }
+        iters_mixed = iters;
     } else {
         B64.alloc(m, npw);
         FS_CUDA(cudaMemcpyAsync(B64.X.p, x0.p, (size_t)m * npw * sizeof(double2), cudaMemcpyDeviceToDevice,
                                 c->stream));
-    }
-    x0.release();
-    bool done = false;
-    if (c->opt.precision == FS_MIXED && status == 1) {
-        // FP64 check of the FP32 result: Y = (H-E)X in FP64 for the wanted
-        // block only, Rayleigh-Ritz on H, FP64 residuals
-        std::vector<double> th(m);
-        FS_CUDA(cudaMemcpyAsync(th.data(), S.s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        FS_CUDA(cudaStreamSynchronize(c->stream));
-        int nw = nstates;
-        while (nw < m && th[nw] <= th[nstates - 1] * (1.0 + 1e-3)) ++nw;
-        S.HE(B64.X.as<double2>(), B64.Y.as<double2>(), nw);
-        S.h_ritz<double2>(B64, th, nres, eps, resid, order);
-        done = true;
-        for (int i : order) done = done && resid[i] <= tol;
+        x0.release();
     }
     if (!done) {
         S.init_block<double2>(B64);
