@@ -227,7 +227,8 @@ def test_folded_solver_matches_lapack(case):
     tol = 1e-8 if case != "box_dense" else 1e-6
     r = of.solve_folded(w, w.e_ref, w.nstates, tol, X0, ham=h)
     assert r["converged"]
-    assert np.abs(r["eps"] - eb).max() < (1e-10 if case != "box_dense" else 1e-9)
+    # compare the sets: the dense box puts E exactly between two levels (a tie in |eps - E|)
+    assert np.abs(np.sort(r["eps"]) - np.sort(eb)).max() < (1e-10 if case != "box_dense" else 1e-9)
     X = r["X"]
     assert np.abs(X.conj() @ X.T - np.eye(w.nstates)).max() < 1e-10
     HX = pw.Hamiltonian(w).apply(X)
