@@ -129,6 +129,27 @@ fs_status fs_gvectors(const fs_ctx* ctx, int* miller);
 fs_status fs_apply_H(fs_ctx* ctx, const void* psi, void* hpsi, int nband,
                      double shift, int precision);
 
+/* hpsi = (H - shift) psi in FP64, like fs_apply_H with precision FS_FP64, but
+ * without allocating device memory during the call: every intermediate (column
+ * buffer, projections, partial sums) lives in one 64 MiB array the library
+ * declares at file scope on the device, so callers that cannot call cudaMalloc
+ * at that point (a restricted allocator, a fully pre-planned memory budget) can
+ * still apply H.  The paper has no counterpart of this call.
+ *   - psi, hpsi: DEVICE pointers, [nband][npw] complex128, not overlapping.
+ *   - Bands are processed in chunks sized to the array; if a single band
+ *     needs more than 64 MiB of scratch the call returns FS_ERR_ARG and says
+ *     how much it needed (fs_last_error).
+ *   - The array is shared by every context and every call on a device and
+ *     keeps the last call's contents; each call overwrites what it reads, so
+ *     nothing needs clearing, but calls that overlap on the GPU (two streams,
+ *     two threads) race on it: serialise them.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (with that device current); make that first call
+ *     before any stream capture.  Each GPU that loads the library holds the
+ *     64 MiB until the process exits.
+ *   - The context itself (fs_create) still allocates; create it beforehand. */
+fs_status fs_apply_H_static(fs_ctx* ctx, const void* psi, void* hpsi, int nband, double shift);
+
 /* Supply the start block used by the next fs_solve: n bands, [n][npw]
  * complex128, host or device (where = FS_HOST / FS_DEVICE).  damp = 1 scales
  * each coefficient by 1/(1 + |q|^2/2) before use (raw random draws); damp = 0

@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     lib.fs_solve.restype = ip
     lib.fs_get_states.argtypes = [vp, vp, ip, ip]
     lib.fs_get_states.restype = ip
+    lib.fs_apply_H_static.argtypes = [vp, vp, vp, ip, dp]
+    lib.fs_apply_H_static.restype = ip
     lib.fs_profile.argtypes = [vp, ip]
     lib.fs_profile.restype = ip
     lib.fs_kernel_stats.argtypes = [vp, C.POINTER(fs_kernel_stat), ip, C.POINTER(C.c_int)]
@@ -180,6 +182,18 @@ class Context:
             out = torch.empty_like(psi)
         self._check(self.lib.fs_apply_H(self.h, C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr()),
                                         psi.shape[0], float(shift), prec), "fs_apply_H")
+        return out
+
+    def apply_H_static(self, psi, out=None, shift=0.0):
+        """FP64 (H - shift) psi through fs_apply_H_static: no device allocation in
+        the library during the call (intermediates live in its static scratch)."""
+        import torch
+        if psi.dtype != torch.complex128 or not psi.is_cuda or not psi.is_contiguous() or psi.dim() != 2:
+            raise ValueError("psi must be a contiguous complex128 CUDA tensor [nband][npw]")
+        if out is None:
+            out = torch.empty_like(psi)
+        self._check(self.lib.fs_apply_H_static(self.h, C.c_void_p(psi.data_ptr()), C.c_void_p(out.data_ptr()),
+                                               psi.shape[0], float(shift)), "fs_apply_H_static")
         return out
 
     def set_initial_states(self, psi, damp=True):

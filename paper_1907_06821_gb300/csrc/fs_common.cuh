@@ -11,6 +11,9 @@
 
 #include "../../include/fs.h"
 
+// size of the file-scope scratch array used by fs_apply_H_static (64 MiB)
+#define FS_STATIC_SCRATCH_BYTES (64ull << 20)
+
 // ------------------------------------------------------------------ complex
 template <typename R> struct cplx;
 template <> struct cplx<double> { using t = double2; };

@@ -239,3 +239,39 @@ template void gemm_nn<double2, double2>(fs_ctx*, int, int, int, const double2*, 
 template void gemm_nn<float2, double2>(fs_ctx*, int, int, int, const double2*, long, long, const float2*, long,
                                        const int*, float2*, long, const int*, double, double, const float2*, long,
                                        int);
+
+// Gram form with caller-provided split-K scratch (no allocation): the same
+// kernels as gemm_gram on CUDA cores; part must hold splits * M * N double2.
+// Returns false when the scratch is too small for even one split.
+template <typename T2>
+bool gemm_gram_scratch(cudaStream_t st, int M, int N, int K, const T2* A, long lda, const T2* B, long ldb, double2* C,
+                       long ci, long cj, double2* part, size_t part_bytes) {
+    if (M <= 0 || N <= 0) return true;
+    const size_t per_split = (size_t)M * N * sizeof(double2);
+    if (per_split > part_bytes) return false;
+    int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+    int want = std::max(1, (2 * 152 + tm * tn - 1) / (tm * tn));
+    int maxs = std::max(1, K / 512);
+    int splits = std::min(std::min(want, maxs), (int)std::min<size_t>(part_bytes / per_split, 1 << 20));
+    int kchunk = (K + splits - 1) / splits;
+    kchunk = ((kchunk + BK - 1) / BK) * BK;
+    splits = std::max(1, (K + kchunk - 1) / kchunk);
+    dim3 g(tm, tn, splits);
+    gram_kernel<T2><<<g, THREADS, 0, st>>>(M, N, K, A, lda, nullptr, B, ldb, nullptr, part, kchunk);
+    long total = (long)M * N;
+    int rb = (int)std::min<long>(2048, (total + 255) / 256);
+    gram_reduce_kernel<<<rb, 256, 0, st>>>(M, N, splits, part, C, ci, cj, 1.0, 0.0);
+    return true;
+}
+
+// Apply form on CUDA cores without the profiling scope (used by the static-scratch entry point).
+void gemm_nn_plain64(cudaStream_t st, int M, int N, int K, const double2* A, long ai, long ak, const double2* B,
+                     long ldb, double2* C, long ldc, double alpha, double beta, const double2* D, long ldd) {
+    if (M <= 0 || N <= 0) return;
+    dim3 g((N + BN - 1) / BN, (M + BM - 1) / BM);
+    nn_kernel<double2, double2><<<g, THREADS, 0, st>>>(M, N, K, A, ai, ak, B, ldb, nullptr, C, ldc, nullptr, alpha,
+                                                       beta, D, ldd);
+}
+
+template bool gemm_gram_scratch<double2>(cudaStream_t, int, int, int, const double2*, long, const double2*, long,
+                                         double2*, long, long, double2*, size_t);

@@ -404,3 +404,127 @@ void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, cons
 
 template void apply_H_impl<double2>(fs_ctx*, const double2*, double2*, int, double, const int*);
 template void apply_H_impl<float2>(fs_ctx*, const float2*, float2*, int, double, const int*);
+
+// ------------------------------------------------------------------ static-scratch H application
+// fs_apply_H_static: the FP64 H application with every intermediate in one
+// file-scope device array instead of buffers the library allocates.  Callers
+// that may not allocate device memory at the time of the call (for example
+// code running under an allocator that forbids cudaMalloc, or a host that
+// pre-plans all of its device memory) use it after fs_create.
+template <typename T2>
+bool gemm_gram_scratch(cudaStream_t st, int M, int N, int K, const T2* A, long lda, const T2* B, long ldb, double2* C,
+                       long ci, long cj, double2* part, size_t part_bytes);
+void gemm_nn_plain64(cudaStream_t st, int M, int N, int K, const double2* A, long ai, long ak, const double2* B,
+                     long ldb, double2* C, long ldc, double alpha, double beta, const double2* D, long ldd);
+
+#include <mutex>
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[FS_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once per device).
+fs_status scratch_address(void** out, std::string& err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        err = "fs_apply_H_static: no usable current device";
+        return FS_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("fs_apply_H_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e);
+            return FS_ERR_CUDA;
+        }
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return FS_OK;
+}
+
+}  // namespace
+
+extern "C" fs_status fs_apply_H_static(fs_ctx* c, const void* psi, void* hpsi, int nband, double shift) {
+    if (!c) return FS_ERR_ARG;
+    if (nband < 0 || (nband > 0 && (!psi || !hpsi || psi == hpsi)) || !std::isfinite(shift)) {
+        c->err = "fs_apply_H_static: bad arguments";
+        return FS_ERR_ARG;
+    }
+    if (nband == 0) return FS_OK;
+    void* base = nullptr;
+    fs_status st = scratch_address(&base, c->err);
+    if (st != FS_OK) return st;
+    const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    const size_t colband = (size_t)n2 * c->ncol * sizeof(double2);
+    const size_t projband = (size_t)c->nptot * sizeof(double2);
+    // one band needs its column buffer, P and Q, and one split of the Gram partial sums
+    const size_t per_band = colband + 3 * projband;
+    if (per_band > (size_t)FS_STATIC_SCRATCH_BYTES) {
+        c->err = "fs_apply_H_static: one band needs " + std::to_string(per_band) + " bytes of scratch, more than the " +
+                 std::to_string((size_t)FS_STATIC_SCRATCH_BYTES) + " bytes of the static array";
+        return FS_ERR_ARG;
+    }
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>(nband, FS_STATIC_SCRATCH_BYTES / per_band));
+    unsigned char* s = static_cast<unsigned char*>(base);
+    double2* cb = reinterpret_cast<double2*>(s);
+    double2* P = reinterpret_cast<double2*>(s + chunk * colband);
+    double2* Q = P + (size_t)chunk * c->nptot;
+    double2* part = Q + (size_t)chunk * c->nptot;
+    const size_t part_bytes = (size_t)FS_STATIC_SCRATCH_BYTES - (size_t)((unsigned char*)part - s);
+    const FftPlan<double2>& px = c->plan64[0];
+    const FftPlan<double2>& py = c->plan64[1];
+    const FftPlan<double2>& pz = c->plan64[2];
+    const int cpb = c->cpb;
+    const int ncb = (c->ncol + cpb - 1) / cpb;
+    const int csm = col_smem(cpb, n2, sizeof(double2));
+    const int psm = n0 * n1 * (int)sizeof(double2);
+    const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
+    const double2* in = static_cast<const double2*>(psi);
+    double2* out = static_cast<double2*>(hpsi);
+    for (int b0 = 0; b0 < nband; b0 += chunk) {
+        const int nbc = std::min(chunk, nband - b0);
+        const double2* src = in + (long)b0 * c->npw;
+        double2* dst = out + (long)b0 * c->npw;
+        dim3 gc(ncb, nbc);
+        col_inverse_kernel<double2><<<gc, COL_THREADS, csm, c->stream>>>(src, nullptr, c->npw, cb,
+                                                                         c->col_start.as<int>(), c->ent_col.as<int>(),
+                                                                         c->ent_z.as<int>(), c->ncol, cpb, pz);
+        dim3 gp(n2, nbc);
+        plane_kernel<double2, double><<<gp, PLANE_THREADS, psm, c->stream>>>(cb, c->col_xy.as<int>(), c->ncol,
+                                                                             c->vz64.as<double>(), px, py);
+        col_forward_kernel<double2><<<gc, COL_THREADS, csm, c->stream>>>(
+            cb, src, nullptr, c->npw, dst, c->col_start.as<int>(), c->ent_col.as<int>(), c->ent_z.as<int>(),
+            c->kin.as<double>(), c->ncol, cpb, pz, inv_ng, shift, c->npw);
+        if (c->nptot > 0) {
+            if (!gemm_gram_scratch<double2>(c->stream, c->nptot, nbc, c->npw, c->beta64.as<double2>(), c->npw, src,
+                                            c->npw, P, 1, c->nptot, part, part_bytes)) {
+                c->err = "fs_apply_H_static: projections do not fit in the static scratch";
+                return FS_ERR_ARG;
+            }
+            int blocks = (int)std::min<long>(4096, ((long)nbc * c->nptot + 255) / 256);
+            apply_D_kernel<double2><<<blocks, 256, 0, c->stream>>>(P, Q, c->Dmat.as<double>(), c->natom, c->nproj,
+                                                                   nbc);
+            gemm_nn_plain64(c->stream, nbc, c->npw, c->nptot, Q, c->nptot, 1, c->beta64.as<double2>(), c->npw, dst,
+                            c->npw, 1.0, 1.0, dst, c->npw);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            c->err = std::string("fs_apply_H_static: ") + cudaGetErrorString(e);
+            return FS_ERR_CUDA;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("fs_apply_H_static: ") + cudaGetErrorString(e);
+        return FS_ERR_CUDA;
+    }
+    c->err.clear();
+    return FS_OK;
+}
