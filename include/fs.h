@@ -185,6 +185,36 @@ typedef struct {
 fs_status fs_profile(fs_ctx* ctx, int enable);
 fs_status fs_kernel_stats(fs_ctx* ctx, fs_kernel_stat* out, int max, int* count);
 
+/* Learned G-shell preconditioner (precond = FS_PREC_LEARNED).  It scales the
+ * paper's G-space diagonal preconditioner M(G) (Sec. II.C) per band and per
+ * kinetic-energy shell of the plane waves:  W_G = M(G) exp(z_{i,s(G)}) R_G,
+ * z = f(features) with f a 4-128-128-128-1 perceptron (tanh hidden layers,
+ * BF16 hidden weights in the forward pass, FP32 arithmetic).  Features of
+ * (band i, shell s): shell centre / ecut, log10 of the shell's share of
+ * |R_i|^2, d_i / 0.1 Ha with d_i = <x_i,(H-E)x_i>, log10 ||R_i|| / 10.  The
+ * untrained network has a zero output layer, i.e. it is exactly M(G).
+ * Parameters: 33,793 floats, W1[128][4] b1 W2[128][128] b2 W3[128][128] b3
+ * W4[128] b4.
+ *
+ * fs_precond_train: solves (e_ref, nstates, tol) once with M(G), solves again
+ * from the same start recording, for each wanted band still iterating, the
+ * residual features and the per-shell log-gain that maps M R onto the
+ * correction into the span of the first solve's states (weight: the shell's
+ * share of |M R|^2); then takes `epochs` full-batch Adam steps (rate lr) on
+ * the weighted squared error and returns the final loss.  Needs a start block
+ * (fs_set_initial_states) or the seeded default.  At most 4 Mi rows are kept. */
+fs_status fs_precond_train(fs_ctx* ctx, double e_ref, int nstates, double tol, int epochs, float lr, float* loss);
+/* rows recorded by the last fs_precond_train */
+fs_status fs_precond_rows(fs_ctx* ctx, long long* nrows);
+/* get (set = 0) or set (set = 1) the n = 33,793 parameters, host float array */
+fs_status fs_precond_weights(fs_ctx* ctx, float* w, int n, int set);
+/* z = f(features) for rows of 4 features; DEVICE arrays [rows][4] and [rows] */
+fs_status fs_precond_eval(fs_ctx* ctx, const float* features, int rows, float* z);
+/* weighted loss sum w (f(x) - t)^2 / sum w (host *loss) and its gradient
+ * (DEVICE grad[33,793]) with respect to the parameters; DEVICE inputs */
+fs_status fs_precond_loss_grad(fs_ctx* ctx, const float* features, const float* target, const float* weight,
+                               int rows, float* loss, float* grad);
+
 /* Release everything the context holds.  NULL is accepted. */
 void fs_destroy(fs_ctx* ctx);
 

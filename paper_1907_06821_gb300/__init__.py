@@ -90,6 +90,16 @@ def load_library(path: str = LIB_PATH):
     lib.fs_get_states.restype = ip
     lib.fs_apply_H_static.argtypes = [vp, vp, vp, ip, dp]
     lib.fs_apply_H_static.restype = ip
+    lib.fs_precond_train.argtypes = [vp, dp, ip, dp, ip, C.c_float, C.POINTER(C.c_float)]
+    lib.fs_precond_train.restype = ip
+    lib.fs_precond_rows.argtypes = [vp, C.POINTER(C.c_longlong)]
+    lib.fs_precond_rows.restype = ip
+    lib.fs_precond_weights.argtypes = [vp, C.POINTER(C.c_float), ip, ip]
+    lib.fs_precond_weights.restype = ip
+    lib.fs_precond_eval.argtypes = [vp, vp, ip, vp]
+    lib.fs_precond_eval.restype = ip
+    lib.fs_precond_loss_grad.argtypes = [vp, vp, vp, vp, ip, C.POINTER(C.c_float), vp]
+    lib.fs_precond_loss_grad.restype = ip
     lib.fs_profile.argtypes = [vp, ip]
     lib.fs_profile.restype = ip
     lib.fs_kernel_stats.argtypes = [vp, C.POINTER(fs_kernel_stat), ip, C.POINTER(C.c_int)]
@@ -229,6 +239,47 @@ class Context:
         self._check(self.lib.fs_get_states(self.h, out.ctypes.data_as(C.c_void_p), n, FS_HOST),
                     "fs_get_states")
         return out
+
+    # ------------------------------------------------ learned preconditioner
+    N_PRECOND_PARAMS = 33793
+
+    def precond_train(self, e_ref, nstates, tol=1e-6, epochs=200, lr=1e-3):
+        """Train the learned G-shell preconditioner from this context's own solves; returns the loss."""
+        loss = C.c_float()
+        self._check(self.lib.fs_precond_train(self.h, float(e_ref), int(nstates), float(tol), int(epochs),
+                                              C.c_float(lr), C.byref(loss)), "fs_precond_train")
+        n = C.c_longlong()
+        self._check(self.lib.fs_precond_rows(self.h, C.byref(n)), "fs_precond_rows")
+        return float(loss.value), int(n.value)
+
+    def precond_weights(self, w=None):
+        """Return the parameters (w None) or set them from a float array."""
+        if w is None:
+            out = np.empty(self.N_PRECOND_PARAMS, dtype=np.float32)
+            self._check(self.lib.fs_precond_weights(self.h, out.ctypes.data_as(C.POINTER(C.c_float)), out.size, 0),
+                        "fs_precond_weights")
+            return out
+        a = np.ascontiguousarray(w, dtype=np.float32)
+        self._check(self.lib.fs_precond_weights(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size, 1),
+                    "fs_precond_weights")
+
+    def precond_eval(self, features):
+        """z = f(features) for a CUDA float32 tensor [rows][4]."""
+        import torch
+        z = torch.empty(features.shape[0], dtype=torch.float32, device=features.device)
+        self._check(self.lib.fs_precond_eval(self.h, C.c_void_p(features.data_ptr()), features.shape[0],
+                                             C.c_void_p(z.data_ptr())), "fs_precond_eval")
+        return z
+
+    def precond_loss_grad(self, features, target, weight):
+        import torch
+        g = torch.empty(self.N_PRECOND_PARAMS, dtype=torch.float32, device=features.device)
+        loss = C.c_float()
+        self._check(self.lib.fs_precond_loss_grad(self.h, C.c_void_p(features.data_ptr()),
+                                                  C.c_void_p(target.data_ptr()), C.c_void_p(weight.data_ptr()),
+                                                  features.shape[0], C.byref(loss), C.c_void_p(g.data_ptr())),
+                    "fs_precond_loss_grad")
+        return float(loss.value), g
 
     def profile(self, enable=True):
         """Reset and start (or stop) per-kernel-class event timing."""

@@ -150,6 +150,27 @@ struct Prof {
     std::vector<cudaEvent_t> pool;
 };
 
+// ------------------------------------------------------------------ learned preconditioner state
+struct Mlp {
+    bool ready = false;
+    int nshell = 32;
+    dbuf shell_of, perm, off;      // shell of each plane wave; plane waves grouped by shell
+    dbuf P, T, m, v, g;            // master params, prepared (BF16, transposed), Adam moments, gradient
+    dbuf gpart, lpart;             // per-block partial gradients / losses
+    dbuf r2, num, den;             // shell sums
+    dbuf F, z;                     // features and outputs of the current iteration
+    dbuf Mdev;                     // the paper's M(G) at e_ref
+    double e_ref = 0;
+    int step = 0;
+    // recording of training rows during a solve
+    bool record = false;
+    int nref = 0;
+    dbuf xref64, xref32;           // reference states [nref][npw]
+    dbuf recF, recz, recw;         // recorded rows
+    long long nrec = 0, cap = 0, nrec_bands = 0;
+    dbuf proj, err;                // work: projections onto the reference span, errors
+};
+
 // ------------------------------------------------------------------ context
 struct fs_ctx {
     // geometry and basis
@@ -203,6 +224,7 @@ struct fs_ctx {
     int nresult = 0;
 
     Prof prof;
+    Mlp mlp;
     dbuf errflag;     // int: set by a device-side wait that gave up
     int gemm_path = 0;
     int tc_gram_kchunk = 1 << 30;  // complex k per tensor-memory accumulation (Gram form)
@@ -261,12 +283,26 @@ template <typename T2>
 void vec_a_resid(fs_ctx* c, const T2* ZR, T2* RH, const T2* X, const double2* dots, const double* theta, int m,
                  double* ra);
 template <typename T2> void vec_row_norms(fs_ctx* c, const T2* X, const int* map, int nrows, double* out);
+template <typename T2> void vec_band_kin(fs_ctx* c, const T2* X, int m, double* out);
 template <typename T2> void vec_scale_rows(fs_ctx* c, T2* X, const int* map, int nrows, const double* nrm);
 template <typename T2>
 void vec_resid_shift(fs_ctx* c, const T2* X, const T2* Y, const double* shift, int m, double* resid);
 void vec_damp_random(fs_ctx* c, double2* X, int m, int first, unsigned long long seed);
 void vec_damp(fs_ctx* c, double2* X, int m);
 template <typename S2, typename T2> void vec_convert(fs_ctx* c, const S2* in, T2* out, size_t count);
+
+// learned preconditioner (fs_mlp.cu)
+int mlp_nparam();
+void mlp_setup(fs_ctx* c);
+void mlp_prepare(fs_ctx* c);
+void mlp_forward(fs_ctx* c, const float* F, int rows, float* z);
+double mlp_loss_grad(fs_ctx* c, const float* F, const float* zt, const float* wt, int rows, double sw);
+void mlp_adam(fs_ctx* c, float lr);
+template <typename T2>
+void mlp_features(fs_ctx* c, const T2* R, const int* act, int na, const double2* dots, const T2* Err, float* F,
+                  float* zt, float* wt);
+template <typename T2> void mlp_make_w(fs_ctx* c, const T2* R, const int* act, int na, T2* W, const double2* dots);
+template <typename T2> void mlp_err_from_proj(fs_ctx* c, const T2* proj, const T2* X, const int* act, int na, T2* E);
 
 // solver (fs_solver.cu)
 fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res);

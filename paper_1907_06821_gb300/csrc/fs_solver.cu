@@ -51,7 +51,7 @@ void swapb(dbuf& a, dbuf& b) {
 }
 
 struct Small {
-    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale;
+    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin;
     int lwork = 0;
     int nbmax = 0;
 };
@@ -160,10 +160,11 @@ struct Solver {
         s.T1.alloc((size_t)nbmax * nbmax * sizeof(double2));
         s.T2.alloc((size_t)nbmax * nbmax * sizeof(double2));
         s.dscale.alloc(nbmax * sizeof(double));
+        s.bkin.alloc(nbmax * sizeof(double));
         s.evals.alloc(nbmax * sizeof(double));
         s.info.alloc(sizeof(int));
         s.theta.alloc(nbmax * sizeof(double));
-        s.act.alloc(nbmax * sizeof(int));
+        s.act.alloc(2 * nbmax * sizeof(int));
         s.resid.alloc(nbmax * sizeof(double));
         s.dots.alloc(nbmax * sizeof(double2));
         s.nrm.alloc(nbmax * sizeof(double));
@@ -403,6 +404,35 @@ struct Solver {
         order.resize(nstates);
     }
 
+    // Training rows for the learned preconditioner: for the wanted bands that are
+    // still active, the A residual (in B.RH) and the correction that would take
+    // the band into the span of the reference states (a converged solve).
+    template <typename T2> void record_pairs(Blocks<T2>& B, const std::vector<int>& act_h) {
+        Mlp& L = c->mlp;
+        std::vector<int> sel;
+        for (int i : act_h)
+            if (i < nstates) sel.push_back(i);
+        const int nr = (int)sel.size();
+        const long long rows = (long long)nr * L.nshell;
+        if (nr == 0 || L.nrec + rows > L.cap) return;
+        const long npw = c->npw;
+        const T2* Xref = sizeof(T2) == 8 ? (const T2*)L.xref32.p : (const T2*)L.xref64.p;
+        int* map = s.act.as<int>() + m;  // second half of the index buffer
+        FS_CUDA(cudaMemcpyAsync(map, sel.data(), nr * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        L.proj.ensure((size_t)nr * npw * sizeof(T2));
+        L.err.ensure((size_t)nr * npw * sizeof(T2));
+        double2* Cg = s.GB.as<double2>();
+        gemm_gram<T2>(c, L.nref, nr, npw, Xref, npw, nullptr, B.X.template as<T2>(), npw, map, Cg, 1, L.nref, 1.0,
+                      0.0);
+        gemm_nn<T2, double2>(c, nr, npw, L.nref, Cg, L.nref, 1, Xref, npw, nullptr, L.proj.template as<T2>(), npw,
+                             nullptr, 1.0, 0.0, nullptr, 0);
+        mlp_err_from_proj<T2>(c, L.proj.template as<T2>(), B.X.template as<T2>(), map, nr, L.err.template as<T2>());
+        mlp_features<T2>(c, B.RH.template as<T2>(), map, nr, s.dots.as<double2>(), L.err.template as<T2>(),
+                         L.recF.as<float>() + L.nrec * 4, L.recz.as<float>() + L.nrec, L.recw.as<float>() + L.nrec);
+        L.nrec += rows;
+        L.nrec_bands += nr;
+    }
+
     // One block iteration on the active set (B.RH holds the A residuals of all bands).
     template <typename T2> void iterate(Blocks<T2>& B, const std::vector<int>& act_h) {
         const int na = (int)act_h.size();
@@ -415,8 +445,15 @@ struct Solver {
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
         // W = M R on the active bands, made orthogonal to X and normalised
-        vec_make_w<T2>(c, B.RH.template as<T2>(), act, na, W, E, c->opt.dE,
-                       c->opt.precond == FS_PREC_TETER ? 1 : 0, nullptr);
+        if (c->mlp.record) record_pairs<T2>(B, act_h);
+        const bool teter = c->opt.precond == FS_PREC_TETER;
+        if (c->opt.precond == FS_PREC_LEARNED) {
+            mlp_make_w<T2>(c, B.RH.template as<T2>(), act, na, W, s.dots.as<double2>());
+        } else {
+            if (teter) vec_band_kin<T2>(c, X, m, s.bkin.as<double>());
+            vec_make_w<T2>(c, B.RH.template as<T2>(), act, na, W, E, c->opt.dE, teter ? 1 : 0,
+                           teter ? s.bkin.as<double>() : nullptr);
+        }
         gemm_gram<T2>(c, m, na, npw, X, npw, nullptr, W, npw, nullptr, GB, 1, m, 1.0, 0.0);
         gemm_nn<T2, double2>(c, na, npw, m, GB, m, 1, X, npw, nullptr, W, npw, nullptr, -1.0, 1.0, W, npw);
         vec_row_norms<T2>(c, W, nullptr, na, s.nrm.as<double>());
@@ -557,6 +594,13 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
     if (m > c->npw) throw fs_error(FS_ERR_ARG, "nstates + guard exceeds the number of plane waves");
     S.ensure_small(3 * m);
     const long npw = c->npw;
+    if (c->opt.precond == FS_PREC_LEARNED || c->mlp.record) {
+        mlp_setup(c);
+        if (c->mlp.e_ref != e_ref || !c->mlp.Mdev.p) {
+            c->mlp.e_ref = e_ref;
+            c->mlp.Mdev.release();
+        }
+    }
     // start block in FP64
     dbuf x0;
     x0.alloc((size_t)m * npw * sizeof(double2));

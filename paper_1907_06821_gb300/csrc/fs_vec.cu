@@ -96,6 +96,24 @@ __global__ void __launch_bounds__(RT) row_norm_kernel(const T2* __restrict__ X, 
     if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
 }
 
+// kinetic energy of each band: sum_g |q_g|^2/2 |x_g|^2 / sum_g |x_g|^2
+template <typename T2>
+__global__ void __launch_bounds__(RT) band_kin_kernel(const T2* __restrict__ X, const double* __restrict__ kin, long npw,
+                                                      double* out) {
+    __shared__ double sh[33];
+    const T2* x = X + (long)blockIdx.x * npw;
+    double s = 0, n = 0;
+    for (long g = threadIdx.x; g < npw; g += blockDim.x) {
+        T2 a = x[g];
+        double p = (double)a.x * a.x + (double)a.y * a.y;
+        s += kin[g] * p;
+        n += p;
+    }
+    s = block_sum(s, sh);
+    n = block_sum(n, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = n > 0 ? s / n : 0.0;
+}
+
 template <typename T2>
 __global__ void scale_rows_kernel(T2* X, const int* __restrict__ map, long npw, const double* __restrict__ nrm) {
     using R = typename real_of<T2>::t;
@@ -272,6 +290,13 @@ template <typename T2> void vec_row_norms(fs_ctx* c, const T2* X, const int* map
     FS_CUDA(cudaGetLastError());
 }
 
+template <typename T2> void vec_band_kin(fs_ctx* c, const T2* X, int m, double* out) {
+    if (m <= 0) return;
+    ProfScope ps(c, KS_VECTOR, 1.0 * m * c->npw * sizeof(T2) + 8.0 * c->npw, 6.0 * m * c->npw);
+    band_kin_kernel<T2><<<m, RT, 0, c->stream>>>(X, c->kin.as<double>(), c->npw, out);
+    FS_CUDA(cudaGetLastError());
+}
+
 template <typename T2> void vec_scale_rows(fs_ctx* c, T2* X, const int* map, int nrows, const double* nrm) {
     if (nrows <= 0) return;
     ProfScope ps(c, KS_VECTOR, 2.0 * nrows * c->npw * sizeof(T2), 2.0 * nrows * c->npw);
@@ -309,6 +334,7 @@ template <typename S2, typename T2> void vec_convert(fs_ctx* c, const S2* in, T2
     template void vec_a_resid<T2>(fs_ctx*, const T2*, T2*, const T2*, const double2*, const double*, int,   \
                                   double*);                                                                 \
     template void vec_row_norms<T2>(fs_ctx*, const T2*, const int*, int, double*);                          \
+    template void vec_band_kin<T2>(fs_ctx*, const T2*, int, double*);                                       \
     template void vec_scale_rows<T2>(fs_ctx*, T2*, const int*, int, const double*);
 INST(double2)
 INST(float2)

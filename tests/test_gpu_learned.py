@@ -1,0 +1,114 @@
+"""Learned G-shell preconditioner on the GPU.
+
+The network's forward pass, loss and gradient (CUDA kernels, FP32 arithmetic,
+BF16 hidden weights) are compared with the FP64 CPU oracle (oracle/mlp.py)
+on weights that BF16 represents exactly; the untrained network must
+reproduce the paper's M(G) run; a network trained on one box is applied to a
+held-out box and must keep the solve correct, and the iteration counts with
+and without it are reported.
+"""
+import numpy as np
+import pytest
+
+import fs_inputs as fi
+from oracle import mlp
+from oracle import planewave as pw
+from gpu_helpers import dense_box
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_1907_06821_gb300 import build as b
+    b.build()
+    import paper_1907_06821_gb300 as m
+    return m
+
+
+def bf16_exact(x):
+    """Round float32 values to the nearest BF16 (ties to even), returned as float32."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((a + 0x7FFF + ((a >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def random_weights(seed):
+    th = mlp.init_params(seed) + 0.1 * np.random.default_rng(seed).normal(size=mlp.n_params())
+    return bf16_exact(th.astype(np.float32))
+
+
+def test_forward_matches_oracle(fs):
+    w = fi.make_config("tiny")
+    with fs.Context.from_workload(w) as c:
+        th = random_weights(4)
+        c.precond_weights(th)
+        assert np.array_equal(c.precond_weights(), th)
+        F = np.random.default_rng(1).normal(size=(1000, 4)).astype(np.float32)
+        z = c.precond_eval(torch.from_numpy(F).cuda()).cpu().numpy()
+        zo, _ = mlp.forward(th.astype(np.float64), F.astype(np.float64))
+        assert np.abs(z - zo).max() <= 1e-4 * max(1.0, np.abs(zo).max())
+
+
+def test_loss_and_gradient_match_oracle(fs):
+    w = fi.make_config("tiny")
+    with fs.Context.from_workload(w) as c:
+        th = random_weights(9)
+        c.precond_weights(th)
+        rng = np.random.default_rng(3)
+        n = 777                                   # several tiles of 28 rows and a ragged tail
+        F = rng.normal(size=(n, 4)).astype(np.float32)
+        zt = rng.normal(size=n).astype(np.float32)
+        wt = rng.uniform(0.0, 1.0, size=n).astype(np.float32)
+        loss, g = c.precond_loss_grad(torch.from_numpy(F).cuda(), torch.from_numpy(zt).cuda(),
+                                      torch.from_numpy(wt).cuda())
+        lo, go = mlp.loss_and_grad(th.astype(np.float64), F.astype(np.float64), zt.astype(np.float64),
+                                   wt.astype(np.float64))
+        g = g.cpu().numpy()
+        assert abs(loss - lo) <= 1e-4 * lo
+        assert np.abs(g - go).max() <= 1e-3 * np.abs(go).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_untrained_network_is_paper_preconditioner(fs, precision):
+    w = fi.make_config("tiny")
+    prec = fs.FS_FP64 if precision == "fp64" else fs.FS_MIXED
+    out = {}
+    for pc in (fs.FS_PREC_M, fs.FS_PREC_LEARNED):
+        with fs.Context.from_workload(w, precision=prec, precond=pc) as c:
+            c.set_initial_states(fi.raw_start_block(w.nbands, c.npw, 17), damp=True)
+            out[pc] = c.solve(w.e_ref, w.nstates, tol=1e-6)
+    a, b = out[fs.FS_PREC_M], out[fs.FS_PREC_LEARNED]
+    assert a["iters"] == b["iters"] and a["n_hpsi"] == b["n_hpsi"]
+    assert np.array_equal(a["eps"], b["eps"])
+
+
+def test_trained_network_on_held_out_box(fs, capsys):
+    """Train on one seeded box, apply to a box of another seed (same sizes)."""
+    train = dense_box()
+    test_box = fi.make_box(L=(16., 16., 24.), n=(24, 24, 36), ecut=4.0, natom=18, widths=(1.0,), nstates=40,
+                           e_ref=None, seed=11)
+    e = np.linalg.eigvalsh(pw.dense_H(test_box))
+    test_box.e_ref = 0.5 * (e[60] + e[61])
+    eb, _, _ = pw.brute_nearest(test_box, test_box.e_ref, test_box.nstates)
+    with fs.Context.from_workload(train, precision=fs.FS_MIXED) as c:
+        c.set_initial_states(fi.raw_start_block(train.nbands, c.npw, 17), damp=True)
+        loss, rows = c.precond_train(train.e_ref, train.nstates, tol=1e-6, epochs=300, lr=2e-3)
+        weights = c.precond_weights()
+    assert rows > 0 and np.isfinite(loss)
+    iters = {}
+    for name, pc in (("M", fs.FS_PREC_M), ("learned", fs.FS_PREC_LEARNED)):
+        with fs.Context.from_workload(test_box, precision=fs.FS_MIXED, precond=pc) as c:
+            if pc == fs.FS_PREC_LEARNED:
+                c.precond_weights(weights)
+            c.set_initial_states(fi.raw_start_block(test_box.nbands, c.npw, 5), damp=True)
+            r = c.solve(test_box.e_ref, test_box.nstates, tol=1e-6)
+            assert r["nconv"] == test_box.nstates
+            assert np.abs(np.sort(r["eps"]) - np.sort(eb)).max() <= 1e-5
+            iters[name] = (r["iters"], r["n_hpsi"])
+    with capsys.disabled():
+        print(f"\n[learned preconditioner] training loss {loss:.4f} on {rows} rows; held-out box: "
+              f"M(G) {iters['M'][0]} iterations / {iters['M'][1]} H applications, "
+              f"learned {iters['learned'][0]} / {iters['learned'][1]}")
+    assert iters["learned"][1] <= 1.5 * iters["M"][1]

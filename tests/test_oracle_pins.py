@@ -266,3 +266,64 @@ def test_pin_catches_dropped_normalisation(monkeypatch):
     g, q = pw.sphere(w.L, w.n, w.ecut, w.k)
     norms = np.sum(np.abs(pw.beta_matrix(w, g, q)) ** 2, axis=0)
     assert not np.allclose(norms, 1.0, atol=1e-3)
+
+
+# ---------------------------------------------------------------- learned preconditioner network
+from oracle import mlp  # noqa: E402
+
+
+def test_mlp_untrained_is_identity_gain():
+    """The output layer starts at zero: z = 0, gain exp(0) = 1, i.e. the paper's M(G)."""
+    th = mlp.init_params(3)
+    F = np.random.default_rng(1).normal(size=(50, 4))
+    z, _ = mlp.forward(th, F)
+    assert np.all(z == 0.0)
+    assert th.size == mlp.n_params() == 33793
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(7)
+    th = mlp.init_params(5) + 0.05 * rng.normal(size=mlp.n_params())
+    F = rng.normal(size=(37, 4))
+    zt = rng.normal(size=37)
+    wt = rng.uniform(0.1, 1.0, size=37)
+    _, g = mlp.loss_and_grad(th, F, zt, wt)
+    for idx in rng.choice(th.size, size=40, replace=False):
+        e = np.zeros_like(th)
+        e[idx] = 1e-6
+        lp, _ = mlp.loss_and_grad(th + e, F, zt, wt)
+        lm, _ = mlp.loss_and_grad(th - e, F, zt, wt)
+        assert abs((lp - lm) / 2e-6 - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))
+
+
+def test_adam_first_step_is_signed_lr():
+    """First Adam step with bias correction moves every parameter by lr*g/(|g|+eps)."""
+    th = np.zeros(5)
+    g = np.array([0.3, -2.0, 1e-3, 0.0, 5.0])
+    new, m, v = mlp.adam_step(th, g, np.zeros(5), np.zeros(5), 1, 0.01)
+    assert np.allclose(new, -0.01 * g / (np.abs(g) + 1e-8))
+
+
+def test_label_recovers_proportional_error():
+    """If the error equals c * M R everywhere, every shell's relative label is 0;
+    if one shell carries twice the gain of the others, its label exceeds theirs
+    by log 2."""
+    rng = np.random.default_rng(2)
+    kin = rng.uniform(0, 5.0, size=400)
+    sh = mlp.shell_index(kin, 5.0, 8)
+    M = 1.0 / ((kin - 0.3) ** 2 + 0.25)
+    R = rng.normal(size=(3, 400)) + 1j * rng.normal(size=(3, 400))
+    c = np.array([0.5, 2.0, 3.0])
+    E_err = c[:, None] * M[None, :] * R
+    F, zt, wt = mlp.features_and_labels(kin, 5.0, 8, M, R, E_err, np.array([0.1, -0.2, 0.0]), sh)
+    z = zt.reshape(3, 8)
+    for i in range(3):
+        # a proportional error is the same gain on every shell: relative label 0
+        assert np.allclose(z[i][wt.reshape(3, 8)[i] > 0], 0.0, atol=1e-12)
+    assert np.allclose(wt.reshape(3, 8).sum(axis=1), 1.0)
+    E2 = E_err.copy()
+    E2[:, sh == 3] *= 2.0
+    _, zt2, wt2 = mlp.features_and_labels(kin, 5.0, 8, M, R, E2, np.array([0.1, -0.2, 0.0]), sh)
+    z2 = zt2.reshape(3, 8)
+    others = [s for s in range(8) if s != 3 and wt2.reshape(3, 8)[0, s] > 0]
+    assert np.allclose(z2[:, 3][:, None] - z2[:, others], np.log(2.0))
