@@ -215,6 +215,26 @@ fs_status fs_precond_eval(fs_ctx* ctx, const float* features, int rows, float* z
 fs_status fs_precond_loss_grad(fs_ctx* ctx, const float* features, const float* target, const float* weight,
                                int rows, float* loss, float* grad);
 
+/* Batched independent boxes (the fragment setting of the paper's LS3DF step,
+ * Sec. II.B: many small problems of uneven size solved independently).  A
+ * batch groups nbox existing contexts, each on its own stream (contexts must
+ * be distinct and must not share a stream), and fs_batch_solve runs their
+ * solves concurrently from nthreads host threads (<= 0: 8) so that the
+ * boxes' kernels overlap on the GPU.  Box i is solved for e_ref[i] and
+ * nstates[i]; res[i].eps / res[i].resid must hold nstates[i] doubles;
+ * status[i] receives each box's status.  The contexts stay owned by the
+ * caller; fs_batch_destroy releases only the grouping. */
+typedef struct fs_batch fs_batch;
+fs_status fs_batch_create(int nbox, fs_ctx* const* ctxs, int nthreads, fs_batch** out);
+fs_status fs_batch_solve(fs_batch* batch, const double* e_ref, const int* nstates, double tol, fs_result* res,
+                         fs_status* status);
+void fs_batch_destroy(fs_batch* batch);
+
+/* FFT tile autotuner: time H applications of 16 bands with 2, 4, 8, 16 and 32
+ * z-columns per thread block for this context's grid and precision, keep the
+ * fastest (cached per grid shape for the process); *cpb receives it (may be NULL). */
+fs_status fs_autotune(fs_ctx* ctx, int* cpb);
+
 /* Release everything the context holds.  NULL is accepted. */
 void fs_destroy(fs_ctx* ctx);
 

@@ -100,6 +100,14 @@ def load_library(path: str = LIB_PATH):
     lib.fs_precond_eval.restype = ip
     lib.fs_precond_loss_grad.argtypes = [vp, vp, vp, vp, ip, C.POINTER(C.c_float), vp]
     lib.fs_precond_loss_grad.restype = ip
+    lib.fs_batch_create.argtypes = [ip, C.POINTER(vp), ip, C.POINTER(vp)]
+    lib.fs_batch_create.restype = ip
+    lib.fs_batch_solve.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int), dp, vp, C.POINTER(C.c_int)]
+    lib.fs_batch_solve.restype = ip
+    lib.fs_batch_destroy.argtypes = [vp]
+    lib.fs_batch_destroy.restype = None
+    lib.fs_autotune.argtypes = [vp, C.POINTER(C.c_int)]
+    lib.fs_autotune.restype = ip
     lib.fs_profile.argtypes = [vp, ip]
     lib.fs_profile.restype = ip
     lib.fs_kernel_stats.argtypes = [vp, C.POINTER(fs_kernel_stat), ip, C.POINTER(C.c_int)]
@@ -281,6 +289,12 @@ class Context:
                     "fs_precond_loss_grad")
         return float(loss.value), g
 
+    def autotune(self):
+        """Pick the FFT column tile for this grid by timing; returns columns per block."""
+        v = C.c_int()
+        self._check(self.lib.fs_autotune(self.h, C.byref(v)), "fs_autotune")
+        return v.value
+
     def profile(self, enable=True):
         """Reset and start (or stop) per-kernel-class event timing."""
         self._check(self.lib.fs_profile(self.h, int(enable)), "fs_profile")
@@ -309,3 +323,47 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Independent boxes solved concurrently (fs_batch_*); the contexts stay owned by the caller."""
+
+    def __init__(self, contexts, nthreads=8):
+        self.lib = load_library()
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.h.value for c in self.contexts])
+        h = C.c_void_p()
+        st = self.lib.fs_batch_create(len(self.contexts), arr, int(nthreads), C.byref(h))
+        if st != FS_OK:
+            raise FSError(st, "fs_batch_create failed")
+        self.h = h
+
+    def solve(self, e_refs, nstates, tol=1e-6):
+        n = len(self.contexts)
+        eps = [np.zeros(k) for k in nstates]
+        res = [np.zeros(k) for k in nstates]
+        results = (fs_result * n)()
+        for i in range(n):
+            results[i].eps = _dptr(eps[i])
+            results[i].resid = _dptr(res[i])
+        e = np.ascontiguousarray(e_refs, dtype=np.float64)
+        ns = np.ascontiguousarray(nstates, dtype=np.int32)
+        status = (C.c_int * n)()
+        self.lib.fs_batch_solve(self.h, _dptr(e), _iptr(ns), float(tol), C.cast(results, C.c_void_p), status)
+        out = []
+        for i in range(n):
+            r = results[i]
+            out.append(dict(eps=eps[i], resid=res[i], nconv=r.nconv, iters=r.iters, n_hpsi=r.n_hpsi,
+                            seconds=r.seconds, status=status[i]))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -171,6 +171,21 @@ struct Mlp {
     dbuf proj, err;                // work: projections onto the reference span, errors
 };
 
+// ------------------------------------------------------------------ solver workspace
+// Kept by the context between solves (allocated on first use, grown when
+// needed, released by fs_destroy), so that repeated and concurrent solves do
+// not allocate or free device memory (cudaFree synchronises the device).
+struct SolverSmall {
+    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin;
+    int lwork = 0;
+    int nbmax = 0;
+};
+struct SolverMem {
+    dbuf b32[12], b64[12];   // band blocks of the FP32 and FP64 stages
+    dbuf x0;                 // start block
+    SolverSmall small;
+};
+
 // ------------------------------------------------------------------ context
 struct fs_ctx {
     // geometry and basis
@@ -225,6 +240,7 @@ struct fs_ctx {
 
     Prof prof;
     Mlp mlp;
+    SolverMem smem;
     dbuf errflag;     // int: set by a device-side wait that gave up
     int gemm_path = 0;
     int tc_gram_kchunk = 1 << 30;  // complex k per tensor-memory accumulation (Gram form)

@@ -279,8 +279,12 @@ static int group_lines(int n, const std::vector<int>& rads, int threads, int ept
     return cap / n;
 }
 
+// The dynamic shared-memory ceiling is a per-kernel attribute shared by every
+// context in the process; it is set once to the device maximum (227 KB) so that
+// contexts with different grids can coexist (each launch asks for what it needs).
 template <typename T2> static void set_attr_smem(const void* fn, int bytes) {
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    (void)bytes;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 void ctx_prepare_fft(fs_ctx* c) {

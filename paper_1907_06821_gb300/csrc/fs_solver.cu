@@ -32,17 +32,19 @@ void ctx_ensure_fp32(fs_ctx* c);
 
 namespace {
 
+// Band blocks, backed by the context's persistent workspace (12 buffers).
 template <typename T2> struct Blocks {
-    dbuf X, Y, W, YW, P, YP, RH, ZR, tX, tY, tP, tYP;
+    dbuf &X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP;
     bool haveP = false;
+    explicit Blocks(dbuf* d)
+        : X(d[0]), Y(d[1]), W(d[2]), YW(d[3]), P(d[4]), YP(d[5]), RH(d[6]), ZR(d[7]), tX(d[8]), tY(d[9]), tP(d[10]),
+          tYP(d[11]) {}
     void alloc(int m, long npw) {
         size_t b = (size_t)m * npw * sizeof(T2);
-        for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->alloc(b);
+        for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->ensure(b);
         haveP = false;
     }
-    void free_all() {
-        for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->release();
-    }
+    void free_all() {}
 };
 
 void swapb(dbuf& a, dbuf& b) {
@@ -50,11 +52,6 @@ void swapb(dbuf& a, dbuf& b) {
     std::swap(a.bytes, b.bytes);
 }
 
-struct Small {
-    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin;
-    int lwork = 0;
-    int nbmax = 0;
-};
 
 __global__ void add_diag_kernel(double2* A, int n, double v) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,7 +140,8 @@ struct Solver {
     double E;
     int nstates, m;
     double tol;
-    Small s;
+    SolverSmall& s;
+    explicit Solver(fs_ctx* c_) : c(c_), s(c_->smem.small) {}
     long long n_hpsi = 0;
     int verbose = 0;
 
@@ -582,8 +580,7 @@ struct Solver {
 
 fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res) {
     auto t0 = std::chrono::steady_clock::now();
-    Solver S;
-    S.c = c;
+    Solver S(c);
     S.E = e_ref;
     S.nstates = nstates;
     S.tol = tol;
@@ -602,8 +599,8 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         }
     }
     // start block in FP64
-    dbuf x0;
-    x0.alloc((size_t)m * npw * sizeof(double2));
+    dbuf& x0 = c->smem.x0;
+    x0.ensure((size_t)m * npw * sizeof(double2));
     int ncopy = std::min(c->ninit, m);
     if (ncopy > 0) {
         FS_CUDA(cudaMemcpyAsync(x0.p, c->init_states.p, (size_t)ncopy * npw * sizeof(double2),
@@ -617,14 +614,13 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
     std::vector<double> eps, resid;
     std::vector<int> order;
     int nres = 0;
-    Blocks<double2> B64;
+    Blocks<double2> B64(c->smem.b64);
     bool done = false;
     if (c->opt.precision == FS_MIXED) {
         ctx_ensure_fp32(c);
-        Blocks<float2> B32;
+        Blocks<float2> B32(c->smem.b32);
         B32.alloc(m, npw);
         vec_convert<double2, float2>(c, x0.as<double2>(), B32.X.as<float2>(), (size_t)m * npw);
-        x0.release();
         S.init_block<float2>(B32);
         B64.alloc(m, npw);
         // FP32 stage to a margin below tol (its residuals carry FP32 noise), then
@@ -655,7 +651,6 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         B64.alloc(m, npw);
         FS_CUDA(cudaMemcpyAsync(B64.X.p, x0.p, (size_t)m * npw * sizeof(double2), cudaMemcpyDeviceToDevice,
                                 c->stream));
-        x0.release();
     }
     if (!done) {
         S.init_block<double2>(B64);

@@ -24,6 +24,7 @@
 #include "fs_common.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace {
 
@@ -498,13 +499,12 @@ __global__ void pack_coef_kernel(const A2* __restrict__ A, long ai, long ak, int
     }
 }
 
-bool g_attr_set = false;
-void set_attrs() {
-    if (g_attr_set) return;
+std::once_flag g_attr_once;
+void set_attrs_once() {
     cudaFuncSetAttribute((const void*)tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     cudaFuncSetAttribute((const void*)tc_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    g_attr_set = true;
 }
+void set_attrs() { std::call_once(g_attr_once, set_attrs_once); }
 
 }  // namespace
 
