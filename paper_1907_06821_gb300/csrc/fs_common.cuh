@@ -176,7 +176,7 @@ struct Mlp {
 // needed, released by fs_destroy), so that repeated and concurrent solves do
 // not allocate or free device memory (cudaFree synchronises the device).
 struct SolverSmall {
-    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin;
+    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin, hres;
     int lwork = 0;
     int nbmax = 0;
 };

@@ -159,6 +159,7 @@ struct Solver {
         s.T2.alloc((size_t)nbmax * nbmax * sizeof(double2));
         s.dscale.alloc(nbmax * sizeof(double));
         s.bkin.alloc(nbmax * sizeof(double));
+        s.hres.alloc(nbmax * sizeof(double));
         s.evals.alloc(nbmax * sizeof(double));
         s.info.alloc(sizeof(int));
         s.theta.alloc(nbmax * sizeof(double));
@@ -335,12 +336,16 @@ struct Solver {
 
     // A residuals R_i = A x_i - theta_i x_i of all bands (left in B.RH), their
     // norms and the Ritz values on the host.  Costs one H application per band.
+    std::vector<double> hres_h;  // H residuals ||y_i - <x_i,y_i> x_i|| of the last a_residuals call
+
     template <typename T2> void a_residuals(Blocks<T2>& B, std::vector<double>& ra, std::vector<double>& th) {
         T2* X = B.X.template as<T2>();
         T2* Y = B.Y.template as<T2>();
         T2* RH = B.RH.template as<T2>();
         T2* ZR = B.ZR.template as<T2>();
-        vec_resid<T2>(c, X, Y, m, s.resid.as<double>(), s.dots.as<double2>());
+        vec_resid<T2>(c, X, Y, m, s.hres.as<double>(), s.dots.as<double2>());
+        hres_h.resize(m);
+        FS_CUDA(cudaMemcpyAsync(hres_h.data(), s.hres.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         vec_rh<T2>(c, X, Y, s.dots.as<double2>(), m, RH);
         HE(RH, ZR, m);
         vec_a_resid<T2>(c, ZR, RH, X, s.dots.as<double2>(), s.theta.as<double>(), m, s.resid.as<double>());
@@ -565,9 +570,14 @@ struct Solver {
                     return 2;
                 }
             }
+            // soft locking: a band stops contributing directions once its A residual
+            // is below the threshold or its own H residual is below half the target
+            // (the FP32 A residual of states close to E has a noise floor; the H
+            // residual of a band that is still a mix of states on both sides of E
+            // stays large, so such a band keeps iterating)
             std::vector<int> act;
             for (int i = 0; i < m; ++i)
-                if (ra[i] > tol_a(th[i], target)) act.push_back(i);
+                if (ra[i] > tol_a(th[i], target) && hres_h[i] > 0.5 * target) act.push_back(i);
             if (act.empty())
                 for (int i = 0; i < m; ++i) act.push_back(i);
             iterate<T2>(B, act);
