@@ -129,9 +129,8 @@ def solve_folded(w, e_ref, nstates, tol, x0_raw, guard=None, dE=0.5, maxit=3000,
         if it == maxit:
             break
         # soft locking: a band stops contributing directions once its A residual
-        # is below its threshold or its own H residual is below half of tol
-        rh = np.linalg.norm(Y - np.sum(X.conj() * Y, axis=1)[:, None] * X, axis=1)
-        act = np.where((ra > tolA) & (rh > 0.5 * tol))[0]
+        # is below its threshold
+        act = np.where(ra > tolA)[0]
         if act.size == 0:
             act = np.arange(m)
         W = M[None, :] * R[act]
