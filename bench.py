@@ -103,10 +103,23 @@ def dist_env():
 
 
 def workload(name, rank):
+    """Rank 0 solves the named seeded instance; every other rank an instance
+    of the same shape with its own seed (independent problems)."""
     import fs_inputs as fi
-    if name == "wire":
-        return fi.make_config("wire", seed=1908 + 1000 * rank) if rank else fi.make_config("wire")
-    return fi.make_config(name)
+    return fi.make_config(name, seed=1908 + 1000 * rank) if rank else fi.make_config(name)
+
+
+def combine_ranks(dist, dev, t_dev, nconv, t_e2e, e2e_states):
+    """Whole-job figures over the ranks: the slowest rank's times and the
+    states converged by all ranks (no collective when dist is None)."""
+    if dist is None:
+        return t_dev, nconv, t_e2e, e2e_states
+    import torch
+    tt = torch.tensor([t_dev, float(nconv), t_e2e, float(e2e_states)], dtype=torch.float64, device=dev)
+    gathered = [torch.zeros_like(tt) for _ in range(dist.get_world_size())]
+    dist.all_gather(gathered, tt)
+    return (max(float(g[0]) for g in gathered), sum(int(g[1]) for g in gathered),
+            max(float(g[2]) for g in gathered), sum(int(g[3]) for g in gathered))
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -207,6 +220,8 @@ def run_ours(args):
     results = [step() for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     clocks = sampler.stop()
     t_dev = ev0.elapsed_time(ev1) / 1e3
     stats = ctx.kernel_stats()
@@ -221,15 +236,7 @@ def run_ours(args):
         e2e_states += r["nconv"]
     t_e2e = time.time() - t0
     nconv = sum(r["nconv"] for r in results)
-    tmax = t_dev
-    if dist:
-        tt = torch.tensor([t_dev, float(nconv), t_e2e, float(e2e_states)], device=dev)
-        gathered = [torch.zeros_like(tt) for _ in range(ws)]
-        dist.all_gather(gathered, tt)
-        tmax = max(float(g[0]) for g in gathered)
-        nconv = sum(int(g[1]) for g in gathered)
-        t_e2e = max(float(g[2]) for g in gathered)
-        e2e_states = sum(int(g[3]) for g in gathered)
+    tmax, nconv, t_e2e, e2e_states = combine_ranks(dist, dev, t_dev, nconv, t_e2e, e2e_states)
     if rank == 0:
         hbm, bf16, smax, src = peaks()
         line = make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, clocks, hbm, bf16, src, ws,

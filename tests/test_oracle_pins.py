@@ -296,6 +296,54 @@ def test_mlp_gradient_matches_finite_differences():
         assert abs((lp - lm) / 2e-6 - g[idx]) <= 1e-6 * max(1.0, abs(g[idx]))
 
 
+def _fd_mismatch(th, F, zt, wt, n=40, seed=11):
+    """Largest |finite difference - backprop| over sampled parameters."""
+    rng = np.random.default_rng(seed)
+    _, g = mlp.loss_and_grad(th, F, zt, wt)
+    worst = 0.0
+    for idx in rng.choice(th.size, size=n, replace=False):
+        e = np.zeros_like(th)
+        e[idx] = 1e-6
+        lp, _ = mlp.loss_and_grad(th + e, F, zt, wt)
+        lm, _ = mlp.loss_and_grad(th - e, F, zt, wt)
+        worst = max(worst, abs((lp - lm) / 2e-6 - g[idx]) / max(1.0, abs(g[idx])))
+    return worst
+
+
+def test_pin_catches_activation_derivative_mismatch(monkeypatch):
+    """Plant a forward activation (sin) that the backward pass's tanh
+    derivative does not match: the finite-difference pin fails."""
+    class _Np:
+        def __getattr__(self, k):
+            return getattr(np, k)
+        tanh = staticmethod(np.sin)
+    rng = np.random.default_rng(7)
+    th = mlp.init_params(5) + 0.05 * rng.normal(size=mlp.n_params())
+    F = rng.normal(size=(37, 4))
+    zt = rng.normal(size=37)
+    wt = rng.uniform(0.1, 1.0, size=37)
+    assert _fd_mismatch(th, F, zt, wt) <= 1e-6
+    monkeypatch.setattr(mlp, "np", _Np())
+    assert _fd_mismatch(th, F, zt, wt) > 1e-4
+
+
+def test_shell_index_matches_brute_force():
+    """Shells are uniform bins of |q|^2/2 over [0, ecut]; the top edge and
+    anything above it fall in the last shell."""
+    rng = np.random.default_rng(4)
+    ecut, ns = 7.5, 9
+    kin = np.concatenate([rng.uniform(0, ecut, 500), [0.0, ecut, ecut * (1 - 1e-12)],
+                          [ecut * s / ns for s in range(1, ns)]])
+    got = mlp.shell_index(kin, ecut, ns)
+    for k, s in zip(kin, got):
+        want = ns - 1
+        for j in range(ns):
+            if ecut * j / ns <= k < ecut * (j + 1) / ns:
+                want = j
+                break
+        assert s == want, (k, s, want)
+
+
 def test_adam_first_step_is_signed_lr():
     """First Adam step with bias correction moves every parameter by lr*g/(|g|+eps)."""
     th = np.zeros(5)
