@@ -175,8 +175,14 @@ struct Mlp {
 // Kept by the context between solves (allocated on first use, grown when
 // needed, released by fs_destroy), so that repeated and concurrent solves do
 // not allocate or free device memory (cudaFree synchronises the device).
+// formatted operand images of the tensor-core apply form: the projector table
+// is kept formatted when its image fits this size; a band block is formatted
+// in chunks of plane-wave tiles of at most the second size
+constexpr size_t FS_TABLE_FMT_MAX_BYTES = 32ull << 30;
+constexpr size_t FS_FMT_CHUNK_BYTES = 4ull << 30;
+
 struct SolverSmall {
-    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin, hres;
+    dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin, hres, keep;
     int lwork = 0;
     int nbmax = 0;
 };
@@ -229,7 +235,12 @@ struct fs_ctx {
     dbuf projbuf;     // [nb][nptot] complex (P)
     dbuf projbuf2;    // [nb][nptot] complex (Q = D P)
     dbuf splitk;      // split-K partial sums
-    dbuf coefbuf;     // float2 coefficients of the tensor-core apply form
+    dbuf beta32_fmt;  // projector table as tensor-core apply-form operand images (formatted once)
+    dbuf afmt;        // apply-form operand images of a band block (per call)
+    dbuf bfmt;        // apply-form coefficient images (per call)
+    dbuf beta32_gfmt; // projector table as Gram-form operand images (formatted once)
+    dbuf gfmt_a;      // Gram-form images of the first operand (per call)
+    dbuf gfmt_b;      // Gram-form images of the second operand with rotated rows (per call)
 
     // solver state
     dbuf init_states; // double2 [ninit][npw]
@@ -244,7 +255,6 @@ struct fs_ctx {
     dbuf errflag;     // int: set by a device-side wait that gave up
     int gemm_path = 0;
     int tc_gram_kchunk = 1 << 30;  // complex k per tensor-memory accumulation (Gram form)
-    int tc_nn_kchunk = 1 << 30;    // complex k per tensor-memory accumulation (apply form)
     std::string err;
 };
 

@@ -15,12 +15,15 @@
 //     UMMA A = rows j' = 2g + c of the 2x2 real blocks [[re, -im], [im, re]]
 //     of B[k][g]; UMMA B = rows i of A(i,k) as (re, im) pairs; D[j'][i] is
 //     component c of C[i][g].
-// Operands are staged by the thread block: global loads run two k-blocks
-// ahead into registers, then each value is split and stored to shared memory
-// in the canonical K-major no-swizzle layout (two stages); one thread issues
-// the MMAs of a stage and commits them to that stage's mbarrier.
+// Formatting kernels first write each operand to global memory as the exact
+// shared-memory images the MMAs read (hi and lo splits, K-major no-swizzle
+// core-matrix layout, 8 complex k per stage); the projector table is
+// formatted once per context.  The GEMM kernels then only move bytes: one
+// thread issues bulk asynchronous copies (cp.async.bulk) into a 4-stage ring,
+// one thread issues the MMAs, and eight warps drain the accumulator.
 // Every mbarrier wait is bounded; on expiry the kernel raises the context's
-// error flag and stops issuing work.
+// error flag, waits (bounded) for its copies and MMAs in flight, releases
+// tensor memory and returns.
 #include "fs_common.cuh"
 
 #include <algorithm>
@@ -28,14 +31,8 @@
 
 namespace {
 
-constexpr int BK = 32;            // FP32 k elements per stage (128 bytes per row)
 constexpr int TM = 128;           // UMMA M (rows of the accumulator = TMEM lanes)
 constexpr int TN_MAX = 256;       // UMMA N maximum
-constexpr int THREADS = 256;
-constexpr int A_BYTES = TM * BK * 4;          // one split of the A tile
-constexpr int B_BYTES = TN_MAX * BK * 4;      // one split of the B tile
-constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 64;
 constexpr long long WAIT_LIMIT = 1ll << 28;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -48,31 +45,8 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
-// byte offset of (row, k) in a K-major tile: 8-row x 16-byte core matrices, K fastest
-__device__ __forceinline__ uint32_t kmaj(int row, int k) {
-    return (uint32_t)((((row >> 3) * (BK / 4) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
-}
-
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)(128 >> 4) << 16;              // leading byte offset: next core matrix along K
-    d |= (uint64_t)(((BK / 4) * 128) >> 4) << 32;  // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;                         // descriptor version
-    return d;                                       // base offset 0, no swizzle
-}
-
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void put2(unsigned char* hi, unsigned char* lo, uint32_t off, float a, float b) {
-    float ah = tf32_rna(a), bh = tf32_rna(b);
-    *reinterpret_cast<float2*>(hi + off) = make_float2(ah, bh);
-    *reinterpret_cast<float2*>(lo + off) = make_float2(tf32_rna(a - ah), tf32_rna(b - bh));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
 }
 
 // bounded wait on a phase parity; returns false on timeout
@@ -120,58 +94,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared machinery: TMEM allocation, the k loop and the drain.
-struct TcCtl {
-    uint64_t* bar;       // [2] one per stage: MMAs reading the stage have completed
-    uint32_t* tslot;     // TMEM address written by tcgen05.alloc
-    unsigned char* st[2];
-};
-
-__device__ __forceinline__ TcCtl tc_setup(unsigned char* smem) {
-    TcCtl t;
-    t.st[0] = smem;
-    t.st[1] = smem + STAGE_BYTES;
-    t.bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);
-    t.tslot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE_BYTES + 32);
-    if (threadIdx.x == 0) {
-        mbar_init(&t.bar[0]);
-        mbar_init(&t.bar[1]);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(t.tslot)),
-                     "r"(TN_MAX));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    return t;
-}
-
-__device__ __forceinline__ void tc_teardown(const TcCtl& t) {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*t.tslot), "r"(TN_MAX));
-    }
-}
-
-// issue the 3 x (BK/8) MMAs of one stage
-__device__ __forceinline__ void tc_issue(const TcCtl& t, int s, uint32_t tmem, uint32_t idesc, bool first) {
-    uint32_t base = smem_u32(t.st[s]);
-    uint32_t ahi = base, alo = base + A_BYTES, bhi = base + 2 * A_BYTES, blo = bhi + B_BYTES;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-    for (int ks = 0; ks < BK / 8; ++ks) {
-        uint32_t o = ks * 256;  // two 16-byte core matrices per K = 8 step
-        mma_tf32(tmem, sdesc(ahi + o), sdesc(bhi + o), idesc, (first && ks == 0) ? 0u : 1u);
-        mma_tf32(tmem, sdesc(ahi + o), sdesc(blo + o), idesc, 1u);
-        mma_tf32(tmem, sdesc(alo + o), sdesc(bhi + o), idesc, 1u);
-    }
-    mma_commit(&t.bar[s]);
-}
-
 // split a 16-byte chunk into hi/lo and store both at byte offset off of (hi, lo)
 __device__ __forceinline__ void put4(unsigned char* hi, unsigned char* lo, uint32_t off, float4 v) {
     float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
@@ -190,177 +112,13 @@ __device__ __forceinline__ float4 load2c(const float2* row, int k, int kend) {
 
 // The accumulation inside tensor memory loses accuracy with the length of
 // the chain (measured: the error of an H application grows about linearly
-// with the number of k-blocks accumulated in place).  Every DRAIN k-blocks
-// the partial tile is read out and added to FP32 registers with ordinary
+// with the number of k-blocks accumulated in place).  Every 128 complex k the
+// partial tile is read out and added to FP32 registers with ordinary
 // round-to-nearest adds, and the next MMA starts a fresh chain.
-constexpr int DRAIN = 8;
-
 // Per thread: TMEM lanes 32 (w & 3) .. +31, columns 128 (w >> 2) .. +127.
 struct Acc {
     float v[4][32];
 };
-
-__device__ __forceinline__ void drain_add(uint32_t tmem, int ncols, Acc& a) {
-    const int w = threadIdx.x >> 5;
-    const int c_base = 128 * (w >> 2);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int c0 = c_base + 32 * j;
-        if (c0 < ncols) {  // warp-uniform
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * (w & 3)) << 16) + c0, v);
-#pragma unroll
-            for (int q = 0; q < 32; ++q) a.v[j][q] += v[q];
-        }
-    }
-}
-
-// One k-block: wait for the stage, store the registers loaded earlier, start
-// the loads two k-blocks ahead, then issue the stage's MMAs.
-template <class P>
-__device__ __forceinline__ bool tc_step(const TcCtl& t, int kb, int nkb, uint32_t tmem, uint32_t idesc, P& p,
-                                        typename P::Regs& r) {
-    const int s = kb & 1;
-    bool ok = true;
-    if (kb >= 2) ok = mbar_wait(&t.bar[s], ((kb - 2) >> 1) & 1);
-    if (!__syncthreads_and(ok)) {
-        // give the MMAs already issued one more bounded chance to finish
-        // before the caller releases tensor memory
-        mbar_wait(&t.bar[(kb - 1) & 1], ((kb - 1) >> 1) & 1);
-        return false;
-    }
-    p.store(r, t.st[s], t.st[s] + A_BYTES, t.st[s] + 2 * A_BYTES, t.st[s] + 2 * A_BYTES + B_BYTES);
-    if (kb + 2 < nkb) p.load(r, kb + 2);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) tc_issue(t, s, tmem, idesc, kb % DRAIN == 0);
-    return true;
-}
-
-// Wait for the MMAs of k-block kb, add the tile to the registers, and make
-// sure every thread has read tensor memory before the next chain overwrites it.
-__device__ __forceinline__ bool tc_drain(const TcCtl& t, int kb, uint32_t tmem, int ncols, Acc& a) {
-    bool ok = mbar_wait(&t.bar[kb & 1], (kb >> 1) & 1);
-    if (!__syncthreads_and(ok)) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    drain_add(tmem, ncols, a);
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    return true;
-}
-
-template <class P>
-__device__ bool tc_run(const TcCtl& t, int nkb, uint32_t tmem, uint32_t idesc, int ncols, P& p, Acc& a) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int q = 0; q < 32; ++q) a.v[j][q] = 0.f;
-    typename P::Regs r0, r1;
-    if (nkb > 0) p.load(r0, 0);
-    if (nkb > 1) p.load(r1, 1);
-    for (int kb = 0; kb < nkb; kb += 2) {
-        if (!tc_step(t, kb, nkb, tmem, idesc, p, r0)) return false;
-        if ((kb % DRAIN == DRAIN - 1 || kb == nkb - 1) && !tc_drain(t, kb, tmem, ncols, a)) return false;
-        if (kb + 1 < nkb) {
-            if (!tc_step(t, kb + 1, nkb, tmem, idesc, p, r1)) return false;
-            if (((kb + 1) % DRAIN == DRAIN - 1 || kb + 1 == nkb - 1) && !tc_drain(t, kb + 1, tmem, ncols, a))
-                return false;
-        }
-    }
-    return true;
-}
-
-// ---------------------------------------------------------------- Gram form
-// part[z][i][j] (float2) = sum over this split's k of conj(A[i][k]) B[j][k]
-struct GramP {
-    const float2* A;
-    long lda;
-    const int* amap;
-    const float2* B;
-    long ldb;
-    const int* bmap;
-    int M, N, i0, j0, nj, kbeg, kend;
-    struct Regs {
-        float4 a[4], b[4];
-    };
-    // A task t in [0, 1024): row (t>>6)*8 + (t&7), chunk (t>>3)&7 -> smem byte 16 t
-    // B task t in [0, 1024): source row (t>>5)*4 + (t&3), chunk (t>>2)&7
-    __device__ __forceinline__ void load(Regs& r, int kb) const {
-        const int kc0 = kbeg + kb * (BK / 2);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = threadIdx.x + THREADS * q;
-            const int row = ((t >> 6) << 3) + (t & 7), ch = (t >> 3) & 7;
-            const int i = i0 + row;
-            r.a[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < M) r.a[q] = load2c(A + (amap ? (long)amap[i] : (long)i) * lda, kc0 + 2 * ch, kend);
-            const int jj = ((t >> 5) << 2) + (t & 3), chb = (t >> 2) & 7;
-            r.b[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (jj < nj) {
-                const int j = j0 + jj;
-                r.b[q] = load2c(B + (bmap ? (long)bmap[j] : (long)j) * ldb, kc0 + 2 * chb, kend);
-            }
-        }
-    }
-    __device__ __forceinline__ void store(const Regs& r, unsigned char* ahi, unsigned char* alo, unsigned char* bhi,
-                                          unsigned char* blo) const {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = threadIdx.x + THREADS * q;
-            put4(ahi, alo, 16u * t, r.a[q]);
-            const int jj = ((t >> 5) << 2) + (t & 3), chb = (t >> 2) & 7;
-            const float4 v = r.b[q];
-            put4(bhi, blo, kmaj(2 * jj, 4 * chb), v);
-            put4(bhi, blo, kmaj(2 * jj + 1, 4 * chb), make_float4(v.y, -v.x, v.w, -v.z));
-        }
-    }
-};
-
-__global__ void __launch_bounds__(THREADS)
-tc_gram_kernel(int M, int N, int K, const float2* __restrict__ A, long lda, const int* __restrict__ amap,
-               const float2* __restrict__ B, long ldb, const int* __restrict__ bmap, float2* __restrict__ part,
-               int kchunk, int* errflag) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    TcCtl t = tc_setup(smem);
-    const uint32_t tmem = *t.tslot;
-    GramP p;
-    p.A = A;
-    p.lda = lda;
-    p.amap = amap;
-    p.B = B;
-    p.ldb = ldb;
-    p.bmap = bmap;
-    p.M = M;
-    p.N = N;
-    p.i0 = blockIdx.x * TM;
-    p.j0 = blockIdx.y * (TN_MAX / 2);
-    p.nj = min(TN_MAX / 2, N - p.j0);
-    p.kbeg = blockIdx.z * kchunk;
-    p.kend = min(K, p.kbeg + kchunk);
-    const int ncols = ((2 * p.nj + 15) / 16) * 16;  // UMMA N
-    const int nkb = (2 * (p.kend - p.kbeg) + BK - 1) / BK;
-    Acc acc;
-    bool ok = tc_run(t, nkb, tmem, idesc_tf32(TM, ncols), ncols, p, acc);
-    if (ok) {
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int i = p.i0 + 32 * (w & 3) + lane;
-        float2* out = part + ((long)blockIdx.z * M + i) * N + p.j0;
-        if (i < M) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c0 = 128 * (w >> 2) + 32 * j;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    int jj = c0 / 2 + q;
-                    if (jj < p.nj) out[jj] = make_float2(acc.v[j][2 * q], acc.v[j][2 * q + 1]);
-                }
-            }
-        }
-    } else if (threadIdx.x == 0) {
-        atomicExch(errflag, 1);
-    }
-    tc_teardown(t);
-}
 
 __global__ void tc_gram_reduce_kernel(int M, int N, int splits, const float2* __restrict__ part, double2* C, long ci,
                                       long cj, double alpha, double beta) {
@@ -384,125 +142,381 @@ __global__ void tc_gram_reduce_kernel(int M, int N, int splits, const float2* __
 }
 
 // ---------------------------------------------------------------- apply form
-// C[ic(i)][g] = alpha sum_k coef[i][k] B[ib(k)][g] + beta D[ic(i)][g], coef compact [M][K] float2
-struct NnP {
-    const float2* B;
-    long ldb;
-    const int* bmap;
-    const float2* coef;
-    int ldk;
-    int N, K, g0, i0, ni, ncols;
-    struct Regs {
-        float4 v[2], c[8];
-    };
-    // UMMA A task t in [0, 512): plane wave g0 + (t & 63), complex k pair t >> 6
-    // UMMA B task t in [0, 2048): coefficient row (t>>6)*8 + (t&7), chunk (t>>3)&7 -> smem byte 16 t
-    __device__ __forceinline__ void load(Regs& r, int kb) const {
-        const int kc0 = kb * (BK / 2);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int t = threadIdx.x + THREADS * q;
-            const int g = g0 + (t & 63), k = kc0 + 2 * (t >> 6);
-            float2 a = make_float2(0.f, 0.f), b = a;
-            if (g < N) {
-                if (k < K) a = __ldg(B + (bmap ? (long)bmap[k] : (long)k) * ldb + g);
-                if (k + 1 < K) b = __ldg(B + (bmap ? (long)bmap[k + 1] : (long)(k + 1)) * ldb + g);
+// C[ic(i)][g] = alpha sum_k A(i,k) B[ib(k)][g] + beta D[ic(i)][g].
+//
+// Both operands are first written to global memory as the exact shared-memory
+// images the MMAs read (TF32 hi and lo splits, K-major core-matrix layout), so
+// the GEMM kernel moves them with bulk asynchronous copies and does no
+// arithmetic on the way in:
+//   UMMA A tile (gt, kb): rows j' = 2g + c of 64 plane waves g, the 8 complex
+//     k of stage kb as 16 reals, the 2x2 real block [[re, -im], [im, re]] of
+//     B[k][g] (row c = 0: (re, -im) pairs, c = 1: (im, re) pairs);
+//   UMMA B tile (it, kb): rows i of the coefficients A(i, k) as (re, im) pairs.
+// The projector table of the nonlocal term is formatted once per context.
+// Kernel roles: warp 0 issues the bulk copies into a 4-stage ring, warp 1
+// issues the MMAs (three per k-step: hi.hi, hi.lo, lo.hi), warps 2-9 drain
+// the tensor-memory accumulator into FP32 registers every 128 complex k, from
+// two accumulator buffers so that the MMAs never wait for the drain.
+constexpr int QK = 16;                        // FP32 k per stage (8 complex k, 64 bytes per row)
+constexpr int QS = 4;                         // stages in the ring
+constexpr int QA_BYTES = TM * QK * 4;         // one split of the A tile (8 KB)
+constexpr int QB_MAX = TN_MAX * QK * 4;       // one split of the largest B tile (16 KB)
+constexpr int QSTAGE = 2 * QA_BYTES + 2 * QB_MAX;
+constexpr int QDRAIN = 16;                    // stages per tensor-memory chain
+constexpr int QTHREADS = 320;
+constexpr int QSMEM = QS * QSTAGE + 128;
+
+__host__ __device__ __forceinline__ uint32_t kmaj16(int row, int k) {
+    return (uint32_t)((((row >> 3) * (QK / 4) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
+}
+
+__device__ __forceinline__ uint64_t sdesc16(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;              // leading byte offset: next core matrix along K
+    d |= (uint64_t)(((QK / 4) * 128) >> 4) << 32;  // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_init_n(uint64_t* bar, int n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(n));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bulk copy global -> shared (16-byte aligned, size a multiple of 16), completion on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// UMMA A tiles of B[k][g]: one thread per (g, pair of complex k)
+// (plane-wave tiles gstart/64 .. +gtiles, written from tile 0 of out)
+__global__ void fmt_expand_kernel(const float2* __restrict__ B, long ldb, const int* __restrict__ bmap, int K, int N,
+                                  int nkb, int gstart, int gtiles, unsigned char* __restrict__ out) {
+    const long ng = (long)gtiles * 64;
+    const long total = ng * nkb * 4;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int gl = (int)(t % ng);
+        const int g = gstart + gl;
+        const int k = 2 * (int)(t / ng);
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (g < N) {
+            if (k < K) a = __ldg(B + (bmap ? (long)bmap[k] : (long)k) * ldb + g);
+            if (k + 1 < K) b = __ldg(B + (bmap ? (long)bmap[k + 1] : (long)(k + 1)) * ldb + g);
+        }
+        const int kb = k >> 3, kq = k & 7, gt = gl >> 6, gg = gl & 63;
+        unsigned char* tile = out + ((size_t)gt * nkb + kb) * (2 * QA_BYTES);
+        put4(tile, tile + QA_BYTES, kmaj16(2 * gg, 2 * kq), make_float4(a.x, -a.y, b.x, -b.y));
+        put4(tile, tile + QA_BYTES, kmaj16(2 * gg + 1, 2 * kq), make_float4(a.y, a.x, b.y, b.x));
+    }
+}
+
+// UMMA B tiles of the coefficients A(i, k) = A[i ai + k ak]: one thread per (i, pair of complex k)
+template <typename A2>
+__global__ void fmt_coef_kernel(const A2* __restrict__ A, long ai, long ak, int M, int K, int TI, int itiles, int nkb,
+                                unsigned char* __restrict__ out) {
+    const long ni = (long)itiles * TI;
+    const long total = ni * nkb * 4;
+    const uint32_t split = (uint32_t)TI * QK * 4;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % ni);
+        const int k = 2 * (int)(t / ni);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < M) {
+            if (k < K) {
+                A2 a = A[i * ai + k * ak];
+                v.x = (float)a.x;
+                v.y = (float)a.y;
             }
-            r.v[q] = make_float4(a.x, a.y, b.x, b.y);
+            if (k + 1 < K) {
+                A2 a = A[i * ai + (k + 1) * ak];
+                v.z = (float)a.x;
+                v.w = (float)a.y;
+            }
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int t = threadIdx.x + THREADS * q;
-            const int row = ((t >> 6) << 3) + (t & 7), ch = (t >> 3) & 7;
-            r.c[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (row < ni) r.c[q] = load2c(coef + (long)(i0 + row) * ldk, kc0 + 2 * ch, K);
-        }
+        const int kb = k >> 3, kq = k & 7, it = i / TI, ii = i - it * TI;
+        unsigned char* tile = out + ((size_t)it * nkb + kb) * (2 * (size_t)split);
+        put4(tile, tile + split, kmaj16(ii, 2 * kq), v);
     }
-    __device__ __forceinline__ void store(const Regs& r, unsigned char* ahi, unsigned char* alo, unsigned char* bhi,
-                                          unsigned char* blo) const {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int t = threadIdx.x + THREADS * q;
-            const int gg = t & 63, kp = t >> 6;
-            const float4 v = r.v[q];  // (re_k, im_k, re_k+1, im_k+1)
-            put4(ahi, alo, kmaj(2 * gg, 4 * kp), make_float4(v.x, -v.y, v.z, -v.w));
-            put4(ahi, alo, kmaj(2 * gg + 1, 4 * kp), make_float4(v.y, v.x, v.w, v.z));
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int t = threadIdx.x + THREADS * q;
-            const int row = ((t >> 6) << 3) + (t & 7);
-            if (row < ncols) put4(bhi, blo, 16u * t, r.c[q]);
-        }
-    }
+}
+
+// Barriers and tensor memory of the bulk-fed kernels (after the QS stages in shared memory).
+struct QCtl {
+    uint64_t* full;   // [QS] stage loaded (bulk-copy transaction bytes)
+    uint64_t* empty;  // [QS] stage consumed by the MMAs
+    uint64_t* accf;   // [2] accumulator chain complete
+    uint64_t* acce;   // [2] accumulator drained by the 8 drain warps
+    uint32_t tmem;
 };
 
-__global__ void __launch_bounds__(THREADS)
-tc_nn_kernel(int M, int N, int K, const float2* __restrict__ coef, int ldk, const float2* __restrict__ B, long ldb,
-             const int* __restrict__ bmap, float2* C, long ldc, const int* __restrict__ cmap, float alpha, float beta,
-             const float2* D, long ldd, int* errflag) {
+__device__ __forceinline__ QCtl tcq_setup(unsigned char* smem) {
+    QCtl t;
+    t.full = reinterpret_cast<uint64_t*>(smem + QS * QSTAGE);
+    t.empty = t.full + QS;
+    t.accf = t.empty + QS;
+    t.acce = t.accf + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(t.acce + 2);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < QS; ++s) {
+            mbar_init_n(&t.full[s], 1);
+            mbar_init_n(&t.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init_n(&t.accf[b], 1);
+            mbar_init_n(&t.acce[b], 8);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    t.tmem = *tslot;
+    return t;
+}
+
+__device__ __forceinline__ void tcq_teardown(const QCtl& t, bool ok, int* errflag) {
+    if (!ok) atomicExch(errflag, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tmem), "r"(512));
+}
+
+// The k loop over nkb stages whose A images (2 x QA_BYTES each) start at a and
+// B images (2 x bsplit each, TI rows) at b.  Warp 0 copies, warp 1 issues
+// the MMAs, warps 2-9 drain; on return the drain threads hold the tile in
+// acc (thread: TMEM lane 32 (warp & 3) + lane, columns 128 ((warp - 2) >> 2)
+// + 32 j + e).  Returns false if a bounded wait gave up.
+__device__ __forceinline__ bool tcq_pipeline(const QCtl& t, unsigned char* smem, const unsigned char* a,
+                                             const unsigned char* b, int nkb, int TI, Acc& acc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bsplit = (uint32_t)TI * QK * 4;
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            int last = -1;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % QS;
+                if (kb >= QS && !mbar_wait(&t.empty[s], ((kb / QS) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = smem + s * QSTAGE;
+                mbar_expect_tx(&t.full[s], 2 * QA_BYTES + 2 * bsplit);
+                bulk_g2s(st, a + (size_t)kb * (2 * QA_BYTES), 2 * QA_BYTES, &t.full[s]);
+                bulk_g2s(st + 2 * QA_BYTES, b + (size_t)kb * (2 * bsplit), 2 * bsplit, &t.full[s]);
+                last = kb;
+            }
+            // every copy issued has landed before the block can exit
+            for (int kb = max(0, last - QS + 1); kb <= last; ++kb)
+                if (!mbar_wait(&t.full[kb % QS], (kb / QS) & 1)) ok = false;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(TM, TI);
+            int last = -1;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % QS, ch = kb / QDRAIN, buf = ch & 1;
+                const bool first = kb % QDRAIN == 0;
+                if (!mbar_wait(&t.full[s], (kb / QS) & 1)) {
+                    ok = false;
+                    break;
+                }
+                if (first && ch >= 2 && !mbar_wait(&t.acce[buf], ((ch >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = smem_u32(smem + s * QSTAGE);
+                const uint32_t ahi = base, alo = base + QA_BYTES, bhi = base + 2 * QA_BYTES, blo = bhi + bsplit;
+                const uint32_t d = t.tmem + (uint32_t)(buf * 256);
+#pragma unroll
+                for (int ks = 0; ks < QK / 8; ++ks) {
+                    const uint32_t o = ks * 256;
+                    mma_tf32(d, sdesc16(ahi + o), sdesc16(bhi + o), idesc, (first && ks == 0) ? 0u : 1u);
+                    mma_tf32(d, sdesc16(ahi + o), sdesc16(blo + o), idesc, 1u);
+                    mma_tf32(d, sdesc16(alo + o), sdesc16(bhi + o), idesc, 1u);
+                }
+                mma_commit(&t.empty[s]);
+                if (kb % QDRAIN == QDRAIN - 1 || kb == nkb - 1) mma_commit(&t.accf[buf]);
+                last = kb;
+            }
+            // the MMAs issued have completed before tensor memory is released
+            if (last >= 0 && !mbar_wait(&t.empty[last % QS], (last / QS) & 1)) ok = false;
+        }
+    } else {
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int nchain = (nkb + QDRAIN - 1) / QDRAIN;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc.v[j][e] = 0.f;
+        for (int ch = 0; ch < nchain; ++ch) {
+            const int buf = ch & 1;
+            if (!mbar_wait(&t.accf[buf], (ch >> 1) & 1)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c0 = 128 * h + 32 * j;
+                if (c0 < TI) {  // warp-uniform
+                    float v[32];
+                    tmem_ld32(t.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256 + c0), v);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) acc.v[j][e] += v[e];
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t.acce[buf]);
+        }
+    }
+    return ok;
+}
+
+__global__ void __launch_bounds__(QTHREADS, 1)
+tcq_nn_kernel(int M, int N, int nkb, int TI, int gt0, const unsigned char* __restrict__ Af,
+              const unsigned char* __restrict__ Bf, float2* C, long ldc, const int* __restrict__ cmap, float alpha,
+              float beta, const float2* D, long ldd, int* errflag) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    TcCtl t = tc_setup(smem);
-    const uint32_t tmem = *t.tslot;
-    NnP p;
-    p.B = B;
-    p.ldb = ldb;
-    p.bmap = bmap;
-    p.coef = coef;
-    p.ldk = ldk;
-    p.N = N;
-    p.K = K;
-    p.g0 = blockIdx.x * (TM / 2);
-    p.i0 = blockIdx.y * TN_MAX;
-    p.ni = min(TN_MAX, M - p.i0);
-    p.ncols = ((p.ni + 15) / 16) * 16;
-    const int nkb = (2 * K + BK - 1) / BK;
+    const QCtl t = tcq_setup(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x, gt = blockIdx.y;
+    const int i0 = it * TI, ni = min(TI, M - i0), g0 = (gt0 + gt) * 64;
     Acc acc;
-    bool ok = tc_run(t, nkb, tmem, idesc_tf32(TM, p.ncols), p.ncols, p, acc);
-    if (ok) {
-        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int r = 32 * (w & 3) + lane;  // j' = 2g + c
-        const int g = p.g0 + (r >> 1);
+    const bool ok = tcq_pipeline(t, smem, Af + (size_t)gt * nkb * (2 * QA_BYTES),
+                                 Bf + (size_t)it * nkb * (2 * (size_t)TI * QK * 4), nkb, TI, acc);
+    if (ok && warp >= 2) {
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int r = 32 * q + lane;  // j' = 2 g + c
+        const int g = g0 + (r >> 1);
         const int comp = r & 1;
         float* Cf = reinterpret_cast<float*>(C);
         const float* Df = reinterpret_cast<const float*>(D);
         if (g < N) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int c0 = 128 * (w >> 2) + 32 * j;
+                const int c0 = 128 * h + 32 * j;
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    int ii = c0 + q;
-                    if (ii < p.ni) {
-                        long row = cmap ? (long)cmap[p.i0 + ii] : (long)(p.i0 + ii);
-                        float o = alpha * acc.v[j][q];
+                for (int e = 0; e < 32; ++e) {
+                    const int ii = c0 + e;
+                    if (ii < ni) {
+                        const long row = cmap ? (long)cmap[i0 + ii] : (long)(i0 + ii);
+                        float o = alpha * acc.v[j][e];
                         if (beta != 0.f) o += beta * Df[(row * ldd + g) * 2 + comp];
                         Cf[(row * ldc + g) * 2 + comp] = o;
                     }
                 }
             }
         }
-    } else if (threadIdx.x == 0) {
-        atomicExch(errflag, 1);
     }
-    tc_teardown(t);
+    tcq_teardown(t, ok, errflag);
 }
 
-// coef[i][k] = A(i, k) as float2, compact
-template <typename A2>
-__global__ void pack_coef_kernel(const A2* __restrict__ A, long ai, long ak, int M, int K, float2* __restrict__ coef) {
-    long total = (long)M * K;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
-        long i = t / K, k = t - i * K;
-        A2 a = A[i * ai + k * ak];
-        coef[t] = make_float2((float)a.x, (float)a.y);
+// ---------------------------------------------------------------- bulk-fed Gram form
+// part[z][i][j] (float2) = sum over the stages of split z of conj(A[ia(i)][k]) B[ib(j)][k].
+// UMMA A tile (it, kb): rows a_i (128 per tile) as (re, im) pairs; UMMA B tile
+// (jt, kb): rows 2j = (re, im) and 2j + 1 = (im, -re) of b_j (TJ rows = TJ/2
+// vectors per tile), so that D[i][2j] = Re C and D[i][2j + 1] = Im C.
+// Formatting: one warp per (8-row group, stage); lane (r = lane & 7, kc =
+// lane >> 3) takes complex k = 8 kb + 2 kc, kc + 1 of row r, and the 8 lanes of
+// one kc write one 128-byte core matrix.
+
+// UMMA A images of rows a_i, stages [kb0, kb0 + nkbl) written as local stages
+__global__ void fmt_rows_kernel(const float2* __restrict__ A, long lda, const int* __restrict__ amap, int M, int K,
+                                int itiles, int kb0, int nkbl, unsigned char* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long nwarp = (long)itiles * 16 * nkbl;
+    for (long w = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; w < nwarp;
+         w += ((long)gridDim.x * blockDim.x) >> 5) {
+        const int rg = (int)(w / nkbl), kbl = (int)(w % nkbl);
+        const int r = lane & 7, kc = lane >> 3;
+        const int i = rg * 8 + r;
+        const int k = (kb0 + kbl) * 8 + 2 * kc;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < M) v = load2c(A + (amap ? (long)amap[i] : (long)i) * lda, k, K);
+        const int it = rg >> 4, rr = ((rg & 15) << 3) + r;
+        unsigned char* tile = out + ((size_t)it * nkbl + kbl) * (2 * QA_BYTES);
+        put4(tile, tile + QA_BYTES, kmaj16(rr, 4 * kc), v);
     }
+}
+
+// UMMA B images of rows b_j with their rotated copies, TJ output rows per tile
+__global__ void fmt_rot_kernel(const float2* __restrict__ B, long ldb, const int* __restrict__ bmap, int N, int K,
+                               int TJ, int jtiles, int nkbl, unsigned char* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long nwarp = (long)jtiles * (TJ / 8) * nkbl;
+    const uint32_t split = (uint32_t)TJ * QK * 4;
+    for (long w = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; w < nwarp;
+         w += ((long)gridDim.x * blockDim.x) >> 5) {
+        const int og = (int)(w / nkbl), kbl = (int)(w % nkbl);
+        const int r = lane & 7, kc = lane >> 3;
+        const int orow = og * 8 + r;
+        const int jt = orow / TJ, rr = orow - jt * TJ;
+        const int j = jt * (TJ / 2) + (rr >> 1);
+        const int k = kbl * 8 + 2 * kc;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < N) v = load2c(B + (bmap ? (long)bmap[j] : (long)j) * ldb, k, K);
+        if (rr & 1) v = make_float4(v.y, -v.x, v.w, -v.z);
+        unsigned char* tile = out + ((size_t)jt * nkbl + kbl) * (2 * (size_t)split);
+        put4(tile, tile + split, kmaj16(rr, 4 * kc), v);
+    }
+}
+
+// grid (itiles, jtiles, splits): split z takes local stages [z kbs, min(nkbl, (z + 1) kbs)) of the
+// chunk; A images of row tile it start at Af + it * astride stages (+ akb0 stages), B images at
+// Bf + jt * nkbl stages; partial sums go to part[(z0 + z) M N + i N + j].
+__global__ void __launch_bounds__(QTHREADS, 1)
+tcq_gram_kernel(int M, int N, int TJ, int nkbl, int kbs, const unsigned char* __restrict__ Af, long astride,
+                long akb0, const unsigned char* __restrict__ Bf, float2* __restrict__ part, int z0, int* errflag) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const QCtl t = tcq_setup(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x, jt = blockIdx.y, z = blockIdx.z;
+    const int kb0 = z * kbs, nk = min(nkbl, kb0 + kbs) - kb0;
+    const int j0 = jt * (TJ / 2), nj = min(TJ / 2, N - j0);
+    Acc acc;
+    const bool ok = tcq_pipeline(t, smem, Af + ((size_t)it * astride + akb0 + kb0) * (2 * QA_BYTES),
+                                 Bf + ((size_t)jt * nkbl + kb0) * (2 * (size_t)TJ * QK * 4), nk, TJ, acc);
+    if (ok && warp >= 2) {
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        const int i = it * TM + 32 * q + lane;
+        if (i < M) {
+            float2* out = part + ((long)(z0 + z) * M + i) * N + j0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c0 = 128 * h + 32 * j;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int jj = c0 / 2 + e;
+                    if (jj < nj) out[jj] = make_float2(acc.v[j][2 * e], acc.v[j][2 * e + 1]);
+                }
+            }
+        }
+    }
+    tcq_teardown(t, ok, errflag);
 }
 
 std::once_flag g_attr_once;
 void set_attrs_once() {
-    cudaFuncSetAttribute((const void*)tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    cudaFuncSetAttribute((const void*)tc_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaFuncSetAttribute((const void*)tcq_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QSMEM);
+    cudaFuncSetAttribute((const void*)tcq_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QSMEM);
 }
 void set_attrs() { std::call_once(g_attr_once, set_attrs_once); }
 
@@ -513,21 +527,74 @@ void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, con
     if (M <= 0 || N <= 0) return;
     set_attrs();
     ProfScope ps(c, kid, ((double)M + N) * K * sizeof(float2) + (double)M * N * sizeof(double2), 8.0 * M * N * K);
-    int tm = (M + TM - 1) / TM, tn = (N + TN_MAX / 2 - 1) / (TN_MAX / 2);
-    int want = std::max(1, (2 * 148 + tm * tn - 1) / (tm * tn));
-    int maxs = std::max(1, K / 1024);
-    int splits = std::min(want, maxs);
-    int kchunk = (K + splits - 1) / splits;
-    kchunk = std::min(kchunk, c->tc_gram_kchunk);
-    kchunk = ((kchunk + BK / 2 - 1) / (BK / 2)) * (BK / 2);
-    splits = std::max(1, (K + kchunk - 1) / kchunk);
-    c->splitk.ensure((size_t)splits * M * N * sizeof(float2));
-    dim3 g(tm, tn, splits);
-    tc_gram_kernel<<<g, THREADS, SMEM_BYTES, c->stream>>>(M, N, K, A, lda, amap, B, ldb, bmap,
-                                                          c->splitk.as<float2>(), kchunk, ctx_errflag(c));
+    const int nkb = std::max(1, (K + 7) / 8);
+    const int itiles = (M + TM - 1) / TM;
+    const int jtiles = (N + TN_MAX / 2 - 1) / (TN_MAX / 2);
+    const int TJ = ((2 * ((N + jtiles - 1) / jtiles)) + 15) / 16 * 16;  // UMMA N, balanced over the tiles
+    const size_t a_stage = (size_t)2 * QA_BYTES;                        // A images of one row tile, one stage
+    const size_t b_stage = (size_t)2 * TJ * QK * 4;
+    auto rows = [&](const unsigned char* dst, int kb0, int nkbl) {
+        const long thr = (long)itiles * 16 * nkbl * 32;
+        fmt_rows_kernel<<<(int)std::min<long>(152 * 16, (thr + 255) / 256), 256, 0, c->stream>>>(
+            A, lda, amap, M, K, itiles, kb0, nkbl, (unsigned char*)dst);
+    };
+    bool table = A == c->beta32.as<float2>() && amap == nullptr && M == c->nptot && K == c->npw;
+    if (table && !c->beta32_gfmt.p && (size_t)itiles * nkb * a_stage <= FS_TABLE_FMT_MAX_BYTES) {
+        c->beta32_gfmt.alloc((size_t)itiles * nkb * a_stage);
+        rows(c->beta32_gfmt.as<unsigned char>(), 0, nkb);
+    }
+    table = table && c->beta32_gfmt.p != nullptr;
+    // stages per chunk of per-call images
+    const size_t per_stage = (table ? 0 : itiles * a_stage) + jtiles * b_stage;
+    const int kchunk = (int)std::max<size_t>(16, std::min<size_t>(nkb, FS_FMT_CHUNK_BYTES / per_stage));
+    const int ntile = itiles * jtiles;
+    std::vector<int> zs;
+    int ztot = 0;
+    for (int kc0 = 0; kc0 < nkb; kc0 += kchunk) {
+        const int nkbl = std::min(kchunk, nkb - kc0);
+        const int want = std::max(1, (2 * 152 + ntile - 1) / ntile);
+        int splits = std::max(1, std::min(want, nkbl / (2 * QDRAIN)));
+        const int kbs = (nkbl + splits - 1) / splits;
+        splits = (nkbl + kbs - 1) / kbs;
+        zs.push_back(splits);
+        ztot += splits;
+    }
+    c->splitk.ensure((size_t)ztot * M * N * sizeof(float2));
+    int z0 = 0, ci_ = 0;
+    for (int kc0 = 0; kc0 < nkb; kc0 += kchunk, ++ci_) {
+        const int nkbl = std::min(kchunk, nkb - kc0);
+        const int splits = zs[ci_];
+        const int kbs = (nkbl + splits - 1) / splits;
+        const unsigned char* Af;
+        long astride, akb0;
+        if (table) {
+            Af = c->beta32_gfmt.as<unsigned char>();
+            astride = nkb;
+            akb0 = kc0;
+        } else {
+            c->gfmt_a.ensure((size_t)itiles * nkbl * a_stage);
+            rows(c->gfmt_a.as<unsigned char>(), kc0, nkbl);
+            Af = c->gfmt_a.as<unsigned char>();
+            astride = nkbl;
+            akb0 = 0;
+        }
+        c->gfmt_b.ensure((size_t)jtiles * nkbl * b_stage);
+        {
+            const float2* Bk = B + (long)kc0 * 8;  // the chunk's first complex k
+            const long thr = (long)jtiles * (TJ / 8) * nkbl * 32;
+            fmt_rot_kernel<<<(int)std::min<long>(152 * 16, (thr + 255) / 256), 256, 0, c->stream>>>(
+                Bk, ldb, bmap, N, K - kc0 * 8, TJ, jtiles, nkbl, c->gfmt_b.as<unsigned char>());
+        }
+        dim3 g(itiles, jtiles, splits);
+        tcq_gram_kernel<<<g, QTHREADS, QSMEM, c->stream>>>(M, N, TJ, nkbl, kbs, Af, astride, akb0,
+                                                           c->gfmt_b.as<unsigned char>(), c->splitk.as<float2>(), z0,
+                                                           ctx_errflag(c));
+        FS_CUDA(cudaGetLastError());
+        z0 += splits;
+    }
     long total = (long)M * N;
     int rb = (int)std::min<long>(2048, (total + 255) / 256);
-    tc_gram_reduce_kernel<<<rb, 256, 0, c->stream>>>(M, N, splits, c->splitk.as<float2>(), C, ci, cj, alpha, beta);
+    tc_gram_reduce_kernel<<<rb, 256, 0, c->stream>>>(M, N, ztot, c->splitk.as<float2>(), C, ci, cj, alpha, beta);
     FS_CUDA(cudaGetLastError());
 }
 
@@ -539,22 +606,42 @@ void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, c
     set_attrs();
     ProfScope ps(c, kid, ((double)K + M * (beta != 0.0 ? 2.0 : 1.0)) * N * sizeof(float2) + (double)M * K * sizeof(A2),
                  8.0 * M * N * K);
-    c->coefbuf.ensure((size_t)M * K * sizeof(float2));
-    long total = (long)M * K;
-    pack_coef_kernel<A2><<<(int)std::min<long>(1024, (total + 255) / 256), 256, 0, c->stream>>>(
-        A, ai, ak, M, K, c->coefbuf.as<float2>());
-    dim3 g((N + TM / 2 - 1) / (TM / 2), (M + TN_MAX - 1) / TN_MAX);
-    // the tensor-memory accumulation runs over at most tc_nn_kchunk complex k
-    // per launch; longer sums continue in FP32 global memory (beta = 1)
-    const int kc = std::max(BK / 2, c->tc_nn_kchunk);
-    for (int k0 = 0; k0 < K; k0 += kc) {
-        const int kk = std::min(kc, K - k0);
-        const bool first = k0 == 0;
-        const int* bm = bmap ? bmap + k0 : nullptr;
-        const float2* Bk = bmap ? B : B + (long)k0 * ldb;
-        tc_nn_kernel<<<g, THREADS, SMEM_BYTES, c->stream>>>(
-            M, N, kk, c->coefbuf.as<float2>() + k0, K, Bk, ldb, bm, C, ldc, cmap, (float)alpha,
-            first ? (float)beta : 1.0f, first ? D : C, first ? ldd : ldc, ctx_errflag(c));
+    const int nkb = std::max(1, (K + 7) / 8);
+    const int itiles = (M + TN_MAX - 1) / TN_MAX;
+    const int TI = (((M + itiles - 1) / itiles) + 15) / 16 * 16;  // balanced tiles, a multiple of 16 columns
+    const int gtiles = (N + 63) / 64;
+    const size_t col_bytes = (size_t)nkb * 2 * QA_BYTES;         // A images of one plane-wave tile
+    auto expand = [&](int gs, int ng, unsigned char* dst) {
+        const long total = (long)ng * 64 * nkb * 4;
+        fmt_expand_kernel<<<(int)std::min<long>(152 * 16, (total + 255) / 256), 256, 0, c->stream>>>(
+            B, ldb, bmap, K, N, nkb, gs * 64, ng, dst);
+    };
+    bool table = B == c->beta32.as<float2>() && bmap == nullptr && N == c->npw && K == c->nptot;
+    if (table && !c->beta32_fmt.p && (size_t)gtiles * col_bytes <= FS_TABLE_FMT_MAX_BYTES) {
+        c->beta32_fmt.alloc((size_t)gtiles * col_bytes);
+        expand(0, gtiles, c->beta32_fmt.as<unsigned char>());
+    }
+    table = table && c->beta32_fmt.p != nullptr;
+    c->bfmt.ensure((size_t)itiles * nkb * 2 * (size_t)TI * QK * 4);
+    {
+        const long total = (long)itiles * TI * nkb * 4;
+        fmt_coef_kernel<A2><<<(int)std::min<long>(152 * 16, (total + 255) / 256), 256, 0, c->stream>>>(
+            A, ai, ak, M, K, TI, itiles, nkb, c->bfmt.as<unsigned char>());
+    }
+    const int chunk = table ? gtiles : (int)std::max<size_t>(1, std::min<size_t>(gtiles, FS_FMT_CHUNK_BYTES / col_bytes));
+    for (int gs = 0; gs < gtiles; gs += chunk) {
+        const int ng = std::min(chunk, gtiles - gs);
+        const unsigned char* Af;
+        if (table) {
+            Af = c->beta32_fmt.as<unsigned char>() + (size_t)gs * col_bytes;
+        } else {
+            c->afmt.ensure((size_t)ng * col_bytes);
+            expand(gs, ng, c->afmt.as<unsigned char>());
+            Af = c->afmt.as<unsigned char>();
+        }
+        dim3 g(itiles, ng);
+        tcq_nn_kernel<<<g, QTHREADS, QSMEM, c->stream>>>(M, N, nkb, TI, gs, Af, c->bfmt.as<unsigned char>(), C, ldc,
+                                                         cmap, (float)alpha, (float)beta, D, ldd, ctx_errflag(c));
         FS_CUDA(cudaGetLastError());
     }
 }

@@ -40,10 +40,11 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--maxit", type=int, default=20)
+    ap.add_argument("--verbose", action="store_true", help="per-iteration solver log on stderr")
     a = ap.parse_args(argv)
     w = fi.make_config(a.workload)
     prec = fs.FS_MIXED if a.precision == "mixed" else fs.FS_FP64
-    ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit)
+    ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit, verbose=int(a.verbose))
     if a.case == "apply":
         dt = torch.complex64 if prec == fs.FS_MIXED else torch.complex128
         X = torch.from_numpy(fi.raw_start_block(a.bands, ctx.npw, 1)).to(dt).cuda()

@@ -130,11 +130,13 @@ def test_solve_matches_lapack(fs, case, precision):
     _check_solution(w, r, states, eb)
 
 
+@pytest.mark.parametrize("nband", [37, 300])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_tensor_core_path_matches_cuda_core_path(fs, case):
-    """FP32 stage: tcgen05 TF32 x3 GEMMs vs FP32 FMA GEMMs on the same input."""
+def test_tensor_core_path_matches_cuda_core_path(fs, case, nband):
+    """FP32 stage: tcgen05 TF32 x3 GEMMs vs FP32 FMA GEMMs on the same input
+    (300 bands: two ragged output tiles of the apply form)."""
     w = CASES[case]()
-    X = fi.raw_start_block(37, pw.sphere(w.L, w.n, w.ecut, w.k)[0].shape[0], 5).astype(np.complex64)
+    X = fi.raw_start_block(nband, pw.sphere(w.L, w.n, w.ecut, w.k)[0].shape[0], 5).astype(np.complex64)
     outs = []
     for path in (fs.FS_GEMM_TENSOR, fs.FS_GEMM_CUDA_CORES):
         with make_ctx(fs, w, precision=fs.FS_MIXED, gemm_path=path) as c:
