@@ -123,6 +123,32 @@ __global__ void min_pivot_kernel(const double2* L, int n, double* out) {
 }
 inline int nblk_(long total) { return nblk(total); }
 
+// out (k x k) = G[keep, keep] for G n x n (all column-major)
+__global__ void gather_sym_kernel(const double2* G, int n, const int* keep, int k, double2* out) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)k * k) return;
+    int i = (int)(t % k), j = (int)(t / k);
+    out[t] = G[keep[i] + (long)keep[j] * n];
+}
+
+// squared diagonal of the Cholesky factor L (k x k) into piv[0..k)
+__global__ void diag_sq_kernel(const double2* L, int k, double* piv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) {
+        double d = L[(long)i * k + i].x;
+        piv[i] = d * d;
+    }
+}
+
+// C (n x m, ld n): row r = U row pos[r] (U k x m, ld k), or 0 where pos[r] < 0
+__global__ void scatter_rows_kernel(double2* C, int n, int m, const double2* U, int k, const int* pos) {
+    long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= (long)n * m) return;
+    int r = (int)(t % n), j = (int)(t / n);
+    int p = pos[r];
+    C[t] = p >= 0 ? U[p + (long)j * k] : make_double2(0.0, 0.0);
+}
+
 // G(i, j) = conj(G(j, i)) where the block of i (boundaries b1 <= b2) is below the block of j
 __global__ void herm_fill_kernel(double2* G, int n, int b1, int b2) {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -168,13 +194,19 @@ struct Solver {
         s.dots.alloc(nbmax * sizeof(double2));
         s.nrm.alloc(nbmax * sizeof(double));
         s.shift.alloc(nbmax * sizeof(double));
-        int lw1 = 0, lw2 = 0;
+        s.keep.alloc(2 * nbmax * sizeof(int));
+        int lw1 = 0, lw2 = 0, lw3 = 0, lw4 = 0, meig = 0;
         FS_SOLVER(cusolverDnZhegvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
                                               CUBLAS_FILL_MODE_LOWER, nbmax, s.GA.as<cuDoubleComplex>(), nbmax,
                                               s.GB.as<cuDoubleComplex>(), nbmax, s.evals.as<double>(), &lw1));
         FS_SOLVER(cusolverDnZheevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nbmax,
                                               s.GA.as<cuDoubleComplex>(), nbmax, s.evals.as<double>(), &lw2));
-        s.lwork = std::max(lw1, lw2);
+        FS_SOLVER(cusolverDnZheevdx_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                               CUBLAS_FILL_MODE_LOWER, nbmax, s.GA.as<cuDoubleComplex>(), nbmax, 0.0,
+                                               0.0, 1, nbmax, &meig, s.evals.as<double>(), &lw3));
+        FS_SOLVER(cusolverDnZpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, nbmax, s.GB.as<cuDoubleComplex>(),
+                                              nbmax, &lw4));
+        s.lwork = std::max(std::max(lw1, lw2), std::max(lw3, lw4));
         s.work.alloc((size_t)s.lwork * sizeof(cuDoubleComplex));
     }
 
@@ -204,40 +236,122 @@ struct Solver {
     // Rayleigh-Ritz of A on a basis of nb vectors with Gram matrices GA = <S, AS>
     // and GB = <S, S> (column-major in s.GA, s.GB).  On return s.GA holds the
     // nb x m coefficients of the m lowest Ritz vectors (column j = vector j)
-    // and s.evals[0..m) their Ritz values.  robust = true selects the basis
-    // by an eigendecomposition of the diagonally scaled GB, dropping the
-    // directions whose eigenvalue is below tau * max (near-dependent vectors
-    // in FP32), instead of a Cholesky factorisation of GB.  Returns the
-    // cuSOLVER info (0 = success).
+    // and s.evals[0..m) their Ritz values.  robust = true scales both matrices
+    // to a unit-diagonal GB and selects the basis by a Cholesky factorisation
+    // of GB that drops every direction whose pivot (squared distance from the
+    // span of the directions before it) is below piv_floor, refactorising
+    // without them; should that not settle, the basis comes from an
+    // eigendecomposition of GB, dropping eigenvalues below tau * max.  Returns
+    // the cuSOLVER info (0 = success).
     int rr_basis(int nb, bool robust, double tau, double piv_floor) {
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
         if (!robust) return hegvd(nb);
         diag_invsqrt_kernel<<<nblk(nb), 256, 0, c->stream>>>(GB, nb, s.dscale.as<double>());
         sym_scale_kernel<<<nblk((long)nb * nb), 256, 0, c->stream>>>(GA, GB, nb, s.dscale.as<double>());
-        {
-            // fast path: Cholesky-based generalized eigensolve of the scaled
-            // problem, accepted when every Cholesky pivot of the unit-diagonal
-            // G_B is above tau (no near-dependent direction)
-            const size_t bytes = (size_t)nb * nb * sizeof(double2);
-            FS_CUDA(cudaMemcpyAsync(s.T1.p, GA, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            FS_CUDA(cudaMemcpyAsync(s.T2.p, GB, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            int info = hegvd(nb);
-            if (info == 0) {
-                min_pivot_kernel<<<1, 256, 0, c->stream>>>(GB, nb, s.nrm.as<double>());
-                double piv = 0;
-                FS_CUDA(cudaMemcpyAsync(&piv, s.nrm.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-                FS_CUDA(cudaStreamSynchronize(c->stream));
-                if (piv > piv_floor) {
-                    row_scale_kernel<<<nblk((long)nb * m), 256, 0, c->stream>>>(GA, nb, m, s.dscale.as<double>());
-                    FS_CUDA(cudaGetLastError());
-                    last_kept = nb;
-                    return 0;
-                }
-            }
-            FS_CUDA(cudaMemcpyAsync(GA, s.T1.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
-            FS_CUDA(cudaMemcpyAsync(GB, s.T2.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        FS_CUDA(cudaGetLastError());
+        std::vector<int> keep(nb);
+        std::iota(keep.begin(), keep.end(), 0);
+        std::vector<double> piv;
+        for (int attempt = 0; attempt < 6 && (int)keep.size() >= m; ++attempt) {
+            const int info = chol_kept(nb, keep, piv);
+            const int k = (int)keep.size();
+            const int valid = info > 0 ? info - 1 : k;  // pivots known before the failing column
+            std::vector<char> drop(k, 0);
+            bool any = info > 0;
+            if (info > 0) drop[info - 1] = 1;
+            for (int i = 0; i < valid; ++i)
+                if (!(piv[i] > piv_floor)) drop[i] = 1, any = true;
+            if (!any) return rr_reduced(nb, keep);
+            std::vector<int> kept;
+            for (int i = 0; i < k; ++i)
+                if (!drop[i]) kept.push_back(keep[i]);
+            keep.swap(kept);
         }
+        return rr_svqb(nb, tau);
+    }
+
+    // Cholesky factor of GB[keep, keep] into s.T2 (k x k) and GA[keep, keep]
+    // into s.T1; squared pivots to piv; returns the potrf info.
+    int chol_kept(int nb, const std::vector<int>& keep, std::vector<double>& piv) {
+        ProfScope ps(c, KS_DENSE_LA, 0.0, 0.0);
+        const int k = (int)keep.size();
+        double2* T1 = s.T1.as<double2>();
+        double2* T2 = s.T2.as<double2>();
+        if (k == nb) {
+            const size_t bytes = (size_t)nb * nb * sizeof(double2);
+            FS_CUDA(cudaMemcpyAsync(T1, s.GA.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            FS_CUDA(cudaMemcpyAsync(T2, s.GB.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            int* kd = s.keep.as<int>();
+            FS_CUDA(cudaMemcpyAsync(kd, keep.data(), k * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            gather_sym_kernel<<<nblk((long)k * k), 256, 0, c->stream>>>(s.GA.as<double2>(), nb, kd, k, T1);
+            gather_sym_kernel<<<nblk((long)k * k), 256, 0, c->stream>>>(s.GB.as<double2>(), nb, kd, k, T2);
+            FS_CUDA(cudaGetLastError());
+        }
+        FS_SOLVER(cusolverDnZpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)T2, k,
+                                   s.work.as<cuDoubleComplex>(), s.lwork, s.info.as<int>()));
+        diag_sq_kernel<<<nblk(k), 256, 0, c->stream>>>(T2, k, s.nrm.as<double>());
+        FS_CUDA(cudaGetLastError());
+        int info = 0;
+        piv.resize(k);
+        FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaMemcpyAsync(piv.data(), s.nrm.p, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        if (info < 0) throw fs_error(FS_ERR_NUMERIC, "potrf argument error " + std::to_string(info));
+        return info;
+    }
+
+    // Standard form of the kept problem, C = L^-1 GA L^-H, its m lowest
+    // eigenpairs, coefficients L^-H V scattered back to the nb rows (rows of
+    // dropped directions 0) and unscaled.
+    int rr_reduced(int nb, const std::vector<int>& keep) {
+        const int k = (int)keep.size();
+        cuDoubleComplex* L = s.T2.as<cuDoubleComplex>();
+        cuDoubleComplex* C = s.T1.as<cuDoubleComplex>();
+        const cuDoubleComplex one = make_cuDoubleComplex(1, 0);
+        int info = 0;
+        {
+            ProfScope ps(c, KS_DENSE_LA, 0.0, 8.0 * k * (double)k * k);
+            FS_BLAS(cublasZtrsm(c->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, k,
+                                k, &one, L, k, C, k));
+            FS_BLAS(cublasZtrsm(c->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT,
+                                k, k, &one, L, k, C, k));
+            int meig = 0;
+            FS_SOLVER(cusolverDnZheevdx(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                        CUBLAS_FILL_MODE_LOWER, k, C, k, 0.0, 0.0, 1, m, &meig, s.evals.as<double>(),
+                                        s.work.as<cuDoubleComplex>(), s.lwork, s.info.as<int>()));
+            FS_BLAS(cublasZtrsm(c->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, k,
+                                m, &one, L, k, C, k));
+            FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            FS_CUDA(cudaStreamSynchronize(c->stream));
+            if (info == 0 && meig != m) info = -2;
+        }
+        if (info != 0) return info;
+        double2* GA = s.GA.as<double2>();
+        if (k == nb) {
+            FS_CUDA(cudaMemcpyAsync(GA, C, (size_t)nb * m * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+            std::vector<int> pos(nb, -1);
+            for (int i = 0; i < k; ++i) pos[keep[i]] = i;
+            int* pd = s.keep.as<int>() + nb;
+            FS_CUDA(cudaMemcpyAsync(pd, pos.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            scatter_rows_kernel<<<nblk((long)nb * m), 256, 0, c->stream>>>(GA, nb, m, (const double2*)C, k, pd);
+        }
+        row_scale_kernel<<<nblk((long)nb * m), 256, 0, c->stream>>>(GA, nb, m, s.dscale.as<double>());
+        FS_CUDA(cudaGetLastError());
+        last_kept = k;
+        ++n_chol_drop[k < nb];
+        return 0;
+    }
+    long long n_chol_drop[2] = {0, 0};  // Rayleigh-Ritz steps without / with dropped directions
+    long long n_svqb = 0;               // steps that needed the eigendecomposition of GB
+
+    // Basis from the eigendecomposition of the scaled GB (s.GA, s.GB scaled).
+    int rr_svqb(int nb, double tau) {
+        double2* GA = s.GA.as<double2>();
+        double2* GB = s.GB.as<double2>();
+        ++n_svqb;
         int info = heevd(nb, GB);
         if (info != 0) return info;
         std::vector<double> lam(nb);
@@ -272,6 +386,7 @@ struct Solver {
         return 0;
     }
     int last_kept = 0;
+    double last_hworst = -1;  // worst wanted H residual of the last H check of run() (-1: none)
 
     template <typename T2> static constexpr bool is_fp32() { return sizeof(T2) == 8; }
     template <typename T2> static double tau_for() { return sizeof(T2) == 8 ? 1e-6 : 1e-11; }
@@ -528,6 +643,7 @@ struct Solver {
             std::vector<double>& eps, std::vector<double>& res, std::vector<int>& order, int& nres) {
         double best = 1e300;
         int since_best = 0;
+        last_hworst = -1;
         std::vector<double> ra, th;
         for (int it = 0;; ++it) {
             if (refresh_every > 0 && it > 0 && it % refresh_every == 0) refresh<T2>(B);
@@ -548,6 +664,7 @@ struct Solver {
                 h_ritz<T2>(B, th, nres, eps, res, order);
                 hworst = 0;
                 for (int i : order) hworst = std::max(hworst, res[i]);
+                last_hworst = hworst;
                 if (hworst <= target) return 1;
             }
             if (verbose)
@@ -634,15 +751,18 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         // FP32 stage to a margin below tol (its residuals carry FP32 noise), then
         // an FP64 check of the wanted bands: Y = (H-E)X in FP64 for those bands
         // only, Rayleigh-Ritz on H with the FP64 overlap, FP64 residuals.  A
-        // failed check tightens the FP32 target; a stalled FP32 stage hands over
-        // to FP64 iterations.
+        // failed check tightens the FP32 target.  A stalled FP32 stage is
+        // checked the same way when its last H check was already within tol;
+        // otherwise, or when that check fails, FP64 iterations take over.
         for (double margin : {0.5, 0.25, 0.125}) {
             status = S.run<float2>(B32, c->opt.maxit - iters, margin * tol, true, iters, 10, eps, resid, order, nres);
             if (S.verbose)
-                fprintf(stderr, "[fs] FP32 stage to %.2f tol: %d iterations, %.2f s, status %d\n", margin, iters,
-                        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), status);
+                fprintf(stderr, "[fs] FP32 stage to %.2f tol: %d iterations, %.2f s, status %d, last H check %.3e\n",
+                        margin, iters, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(),
+                        status, S.last_hworst);
             vec_convert<float2, double2>(c, B32.X.as<float2>(), B64.X.as<double2>(), (size_t)m * npw);
-            if (status != 1) break;
+            const bool stalled_close = status == 2 && S.last_hworst >= 0 && S.last_hworst <= tol;
+            if (status != 1 && !stalled_close) break;
             std::vector<double> th(m);
             FS_CUDA(cudaMemcpyAsync(th.data(), S.s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
             FS_CUDA(cudaStreamSynchronize(c->stream));
@@ -652,7 +772,9 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
             S.h_ritz<double2>(B64, th, nres, eps, resid, order);
             done = true;
             for (int i : order) done = done && resid[i] <= tol;
-            if (done || iters >= c->opt.maxit) break;
+            if (S.verbose)
+                fprintf(stderr, "[fs] FP64 check of the FP32 result: %s\n", done ? "passed" : "failed");
+            if (done || iters >= c->opt.maxit || status != 1) break;
         }
         iters_mixed = iters;
     } else {
@@ -671,8 +793,10 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         S.h_ritz<double2>(B64, th, nres, eps, resid, order);
     }
     if (S.verbose)
-        fprintf(stderr, "[fs] done: %d iterations, %.2f s\n", iters,
-                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+        fprintf(stderr, "[fs] done: %d iterations, %.2f s; Rayleigh-Ritz bases: %lld full, %lld with dropped "
+                        "directions, %lld by eigendecomposition\n", iters,
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(), S.n_chol_drop[0],
+                S.n_chol_drop[1], S.n_svqb);
     c->result_states.ensure((size_t)nstates * npw * sizeof(double2));
     int nconv = 0;
     for (int i = 0; i < nstates; ++i) {
