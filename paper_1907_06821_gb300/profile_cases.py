@@ -2,6 +2,12 @@
 
     python -m paper_1907_06821_gb300.profile_cases apply --workload wire --bands 64 --precision mixed
     python -m paper_1907_06821_gb300.profile_cases solve --workload wire --maxit 20
+    python -m paper_1907_06821_gb300.profile_cases apply --workload medium --bands 64
+
+``medium`` is a 24 x 24 x 48 bohr box on a 48 x 48 x 96 grid at 20 Ry (41,657
+plane waves) with 64 wells and 8 projectors per atom: operands larger than the
+L2 cache with about 2 GB on the device, for captures that replay a kernel many
+times.
 
 ``apply`` builds the context and applies (H - E) to a block of seeded random
 bands ``--repeat`` times (the first two launches warm up); ``solve`` runs a
@@ -35,14 +41,18 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["apply", "solve"])
-    ap.add_argument("--workload", default="wire", choices=["tiny", "wire"])
+    ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "medium"])
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--maxit", type=int, default=20)
     ap.add_argument("--verbose", action="store_true", help="per-iteration solver log on stderr")
     a = ap.parse_args(argv)
-    w = fi.make_config(a.workload)
+    if a.workload == "medium":
+        w = fi.make_box(L=(24.0, 24.0, 48.0), n=(48, 48, 96), ecut=10.0, natom=64, widths=(0.8, 1.2),
+                        lattice=5.0, nstates=128, e_ref=0.05, seed=11, name="medium")
+    else:
+        w = fi.make_config(a.workload)
     prec = fs.FS_MIXED if a.precision == "mixed" else fs.FS_FP64
     ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit, verbose=int(a.verbose))
     if a.case == "apply":
