@@ -133,8 +133,32 @@ enum {
     KS_ROTATE,       // solver basis rotations and projections
     KS_VECTOR,       // residuals, preconditioner, norms, scaling
     KS_DENSE_LA,     // FP64 small dense eigensolves and products
+    // the same work in FP64 (FP64 stage and the FP64 check of the FP32 result)
+    KS_COL_INV64,
+    KS_PLANE64,
+    KS_COL_FWD64,
+    KS_NL_PROJ64,
+    KS_NL_ADD64,
+    KS_GRAM64,
+    KS_ROTATE64,
+    KS_VECTOR64,
     KS_COUNT
 };
+// class of a step in the arithmetic of T2 (FP64 steps are counted apart)
+template <typename T2> constexpr int ks_prec(int id) {
+    if (sizeof(T2) != 16) return id;
+    switch (id) {
+        case KS_COL_INV: return KS_COL_INV64;
+        case KS_PLANE: return KS_PLANE64;
+        case KS_COL_FWD: return KS_COL_FWD64;
+        case KS_NL_PROJ: return KS_NL_PROJ64;
+        case KS_NL_ADD: return KS_NL_ADD64;
+        case KS_GRAM: return KS_GRAM64;
+        case KS_ROTATE: return KS_ROTATE64;
+        case KS_VECTOR: return KS_VECTOR64;
+        default: return id;
+    }
+}
 struct KStat {
     long long launches = 0;
     double ms = 0, bytes = 0, flops = 0;

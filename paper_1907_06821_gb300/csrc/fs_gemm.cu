@@ -194,7 +194,8 @@ void gemm_gram(fs_ctx* c, int M, int N, int K, const T2* A, long lda, const int*
             return;
         }
     }
-    ProfScope ps(c, kid, ((double)M + N) * K * sizeof(T2) + (double)M * N * sizeof(double2), 8.0 * M * N * K);
+    ProfScope ps(c, ks_prec<T2>(kid), ((double)M + N) * K * sizeof(T2) + (double)M * N * sizeof(double2),
+                 8.0 * M * N * K);
     int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
     int want = std::max(1, (2 * 152 + tm * tn - 1) / (tm * tn));
     int maxs = std::max(1, K / 512);
@@ -221,7 +222,7 @@ void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, cons
             return;
         }
     }
-    ProfScope ps(c, kid, ((double)K + M * (beta != 0.0 ? 2.0 : 1.0)) * N * sizeof(T2) + (double)M * K * sizeof(A2),
+    ProfScope ps(c, ks_prec<T2>(kid), ((double)K + M * (beta != 0.0 ? 2.0 : 1.0)) * N * sizeof(T2) + (double)M * K * sizeof(A2),
                  8.0 * M * N * K);
     dim3 g((N + BN - 1) / BN, (M + BM - 1) / BM);
     nn_kernel<T2, A2><<<g, THREADS, 0, c->stream>>>(M, N, K, A, ai, ak, B, ldb, bmap, C, ldc, cmap, alpha, beta, D,

@@ -367,19 +367,19 @@ void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, cons
         const double ng = (double)n0 * n1 * n2;
         dim3 gc(ncb, nbc);
         {
-        ProfScope ps(c, KS_COL_INV, sphb + colb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
+        ProfScope ps(c, ks_prec<T2>(KS_COL_INV), sphb + colb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
         col_inverse_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(src, rm, c->npw, cb, c->col_start.as<int>(),
                                                                      c->ent_col.as<int>(), c->ent_z.as<int>(),
                                                                      c->ncol, cpb, pz);
         }
         dim3 gp(n2, nbc);
         {
-        ProfScope ps(c, KS_PLANE, 2.0 * colb + ng * sizeof(R), 2.0 * 5.0 * nbc * ng * std::log2((double)n0 * n1));
+        ProfScope ps(c, ks_prec<T2>(KS_PLANE), 2.0 * colb + ng * sizeof(R), 2.0 * 5.0 * nbc * ng * std::log2((double)n0 * n1));
         plane_kernel<T2, R><<<gp, PLANE_THREADS, psm, c->stream>>>(cb, c->col_xy.as<int>(), c->ncol,
                                                                    (const R*)vz_of<T2>(c), px, py);
         }
         {
-        ProfScope ps(c, KS_COL_FWD, colb + 2.0 * sphb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
+        ProfScope ps(c, ks_prec<T2>(KS_COL_FWD), colb + 2.0 * sphb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
         col_forward_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(
             cb, src, rm, c->npw, hpsi + (long)b0 * c->npw, c->col_start.as<int>(), c->ent_col.as<int>(),
             c->ent_z.as<int>(), c->kin.as<double>(), c->ncol, cpb, pz, inv_ng, shift, c->npw);
@@ -392,7 +392,7 @@ void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, cons
         c->projbuf2.ensure((size_t)nb * c->nptot * sizeof(double2));
         double2* P = c->projbuf.as<double2>();
         gemm_gram<T2>(c, c->nptot, nb, c->npw, beta_of<T2>(c), c->npw, nullptr, psi, c->npw, rowmap, P, 1,
-                      c->nptot, 1.0, 0.0, KS_NL_PROJ);
+                      c->nptot, 1.0, 0.0, ks_prec<T2>(KS_NL_PROJ));
         double2* Q = c->projbuf2.as<double2>();
         int blocks = (int)std::min<long>(4096, ((long)nb * c->nptot + 255) / 256);
         {
@@ -402,7 +402,7 @@ void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, cons
         FS_CUDA(cudaGetLastError());
         // hpsi[b][g] += sum_p Q[b][p] beta[p][g]
         gemm_nn<T2, double2>(c, nb, c->npw, c->nptot, Q, c->nptot, 1, beta_of<T2>(c), c->npw, nullptr, hpsi,
-                             c->npw, nullptr, 1.0, 1.0, hpsi, c->npw, KS_NL_ADD);
+                             c->npw, nullptr, 1.0, 1.0, hpsi, c->npw, ks_prec<T2>(KS_NL_ADD));
     }
 }
 

@@ -7,7 +7,9 @@ namespace {
 const char* const KS_NAMES[KS_COUNT] = {"col_inverse_fft", "plane_fft_vloc", "col_forward_fft",
                                         "nonlocal_project", "nonlocal_D",    "nonlocal_add",
                                         "gram",            "rotate",         "vector",
-                                        "dense_la"};
+                                        "dense_la",        "col_inverse_fft_fp64", "plane_fft_vloc_fp64",
+                                        "col_forward_fft_fp64", "nonlocal_project_fp64", "nonlocal_add_fp64",
+                                        "gram_fp64",       "rotate_fp64",    "vector_fp64"};
 
 cudaEvent_t take(fs_ctx* c) {
     if (!c->prof.pool.empty()) {

@@ -242,7 +242,7 @@ inline int gx_for(long npw) { return (int)std::min<long>(64, (npw + 255) / 256);
 
 template <typename T2> void vec_resid(fs_ctx* c, const T2* X, const T2* Y, int m, double* resid, double2* dot) {
     if (m <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 2.0 * m * c->npw * sizeof(T2), 16.0 * m * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 2.0 * m * c->npw * sizeof(T2), 16.0 * m * c->npw);
     resid_kernel<T2><<<m, RT, 0, c->stream>>>(X, Y, c->npw, resid, dot);
     FS_CUDA(cudaGetLastError());
 }
@@ -250,7 +250,7 @@ template <typename T2> void vec_resid(fs_ctx* c, const T2* X, const T2* Y, int m
 template <typename T2>
 void vec_resid_shift(fs_ctx* c, const T2* X, const T2* Y, const double* shift, int m, double* resid) {
     if (m <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 2.0 * m * c->npw * sizeof(T2), 8.0 * m * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 2.0 * m * c->npw * sizeof(T2), 8.0 * m * c->npw);
     resid_shift_kernel<T2><<<m, RT, 0, c->stream>>>(X, Y, shift, c->npw, resid);
     FS_CUDA(cudaGetLastError());
 }
@@ -259,7 +259,7 @@ template <typename T2>
 void vec_make_w(fs_ctx* c, const T2* R, const int* act, int na, T2* W, double e_ref, double dE, int precond,
                 const double* band_kin) {
     if (na <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 2.0 * na * c->npw * sizeof(T2) + c->npw * 8.0, 6.0 * na * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 2.0 * na * c->npw * sizeof(T2) + c->npw * 8.0, 6.0 * na * c->npw);
     dim3 g(gx_for(c->npw), na);
     make_w_kernel<T2><<<g, 256, 0, c->stream>>>(R, act, c->npw, W, c->kin.as<double>(), e_ref, dE * dE, precond,
                                                  band_kin);
@@ -268,7 +268,7 @@ void vec_make_w(fs_ctx* c, const T2* R, const int* act, int na, T2* W, double e_
 
 template <typename T2> void vec_rh(fs_ctx* c, const T2* X, const T2* Y, const double2* dots, int m, T2* RH) {
     if (m <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 3.0 * m * c->npw * sizeof(T2), 8.0 * m * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 3.0 * m * c->npw * sizeof(T2), 8.0 * m * c->npw);
     dim3 g(gx_for(c->npw), m);
     rh_kernel<T2><<<g, 256, 0, c->stream>>>(X, Y, dots, c->npw, RH);
     FS_CUDA(cudaGetLastError());
@@ -278,28 +278,28 @@ template <typename T2>
 void vec_a_resid(fs_ctx* c, const T2* ZR, T2* RH, const T2* X, const double2* dots, const double* theta, int m,
                  double* ra) {
     if (m <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 4.0 * m * c->npw * sizeof(T2), 20.0 * m * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 4.0 * m * c->npw * sizeof(T2), 20.0 * m * c->npw);
     a_resid_kernel<T2><<<m, RT, 0, c->stream>>>(ZR, RH, X, dots, theta, c->npw, ra);
     FS_CUDA(cudaGetLastError());
 }
 
 template <typename T2> void vec_row_norms(fs_ctx* c, const T2* X, const int* map, int nrows, double* out) {
     if (nrows <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 1.0 * nrows * c->npw * sizeof(T2), 4.0 * nrows * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 1.0 * nrows * c->npw * sizeof(T2), 4.0 * nrows * c->npw);
     row_norm_kernel<T2><<<nrows, RT, 0, c->stream>>>(X, map, c->npw, out);
     FS_CUDA(cudaGetLastError());
 }
 
 template <typename T2> void vec_band_kin(fs_ctx* c, const T2* X, int m, double* out) {
     if (m <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 1.0 * m * c->npw * sizeof(T2) + 8.0 * c->npw, 6.0 * m * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 1.0 * m * c->npw * sizeof(T2) + 8.0 * c->npw, 6.0 * m * c->npw);
     band_kin_kernel<T2><<<m, RT, 0, c->stream>>>(X, c->kin.as<double>(), c->npw, out);
     FS_CUDA(cudaGetLastError());
 }
 
 template <typename T2> void vec_scale_rows(fs_ctx* c, T2* X, const int* map, int nrows, const double* nrm) {
     if (nrows <= 0) return;
-    ProfScope ps(c, KS_VECTOR, 2.0 * nrows * c->npw * sizeof(T2), 2.0 * nrows * c->npw);
+    ProfScope ps(c, ks_prec<T2>(KS_VECTOR), 2.0 * nrows * c->npw * sizeof(T2), 2.0 * nrows * c->npw);
     dim3 g(gx_for(c->npw), nrows);
     scale_rows_kernel<T2><<<g, 256, 0, c->stream>>>(X, map, c->npw, nrm);
     FS_CUDA(cudaGetLastError());
