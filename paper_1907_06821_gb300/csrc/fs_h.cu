@@ -75,6 +75,12 @@ template <typename T2> struct Bfly<T2, 5> {
     }
 };
 
+// q = a / d (integer quotient) for 0 <= a < 2^22, d >= 1, without an integer
+// division: (a + 1/2) / d = q + (r + 1/2) / d lies at least 1/(2d) from the
+// nearest integer, and the float product (a + 1/2) fl(1/d) differs from it by
+// less than (a + 1/2) 2^-23 / d < 1/(2d), so truncation gives q exactly.
+__device__ __forceinline__ int qdiv(int a, float inv_d) { return (int)(((float)a + 0.5f) * inv_d); }
+
 // One Stockham stage over `nl` lines of length n held in shared memory.
 // All reads of the stage are staged in registers before any write, so the
 // stage runs in place.  KM butterflies per thread must cover nl * n / R.
@@ -83,15 +89,17 @@ __device__ __forceinline__ void fft_stage(T2* buf, int n, int nl, int lstride, i
                                           const T2* __restrict__ tw, int sign) {
     const int nb = n / R;
     const int total = nb * nl;
+    const float inb = 1.0f / (float)nb, ins = 1.0f / (float)Ns;
+    const int wstep = n / (Ns * R);
     T2 v[KM][R];
 #pragma unroll
     for (int kk = 0; kk < KM; ++kk) {
         int t = threadIdx.x + kk * blockDim.x;
         if (t < total) {
-            int line = t / nb, j = t - line * nb;
+            int line = qdiv(t, inb), j = t - line * nb;
             const T2* base = buf + (long)line * lstride;
-            int tj = j % Ns;
-            int step = (n / (Ns * R)) * tj;
+            int tj = j - qdiv(j, ins) * Ns;
+            int step = wstep * tj;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 T2 x = base[(j + r * nb) * estride];
@@ -110,10 +118,10 @@ __device__ __forceinline__ void fft_stage(T2* buf, int n, int nl, int lstride, i
     for (int kk = 0; kk < KM; ++kk) {
         int t = threadIdx.x + kk * blockDim.x;
         if (t < total) {
-            int line = t / nb, j = t - line * nb;
+            const int line = qdiv(t, inb), j = t - line * nb;
             T2* base = buf + (long)line * lstride;
-            int tj = j % Ns;
-            int idxD = (j / Ns) * Ns * R + tj;
+            const int jq = qdiv(j, ins), tj = j - jq * Ns;
+            int idxD = jq * Ns * R + tj;
 #pragma unroll
             for (int r = 0; r < R; ++r) base[(idxD + r * Ns) * estride] = v[kk][r];
         }
