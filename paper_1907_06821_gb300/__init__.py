@@ -120,6 +120,11 @@ def load_library(path: str = LIB_PATH):
     return lib
 
 
+def _torch_c128():
+    import torch
+    return torch.complex128
+
+
 def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -215,14 +220,18 @@ class Context:
         return out
 
     def set_initial_states(self, psi, damp=True):
-        """Start block [n][npw] complex128: a numpy array (host) or a CUDA tensor."""
+        """Start block [n][npw] complex128: a numpy array or CPU tensor (host, e.g. pinned)
+        or a CUDA tensor (device)."""
         if isinstance(psi, np.ndarray):
             a = np.ascontiguousarray(psi, dtype=np.complex128)
             self._check(self.lib.fs_set_initial_states(self.h, a.ctypes.data_as(C.c_void_p), a.shape[0],
                                                        int(damp), FS_HOST), "fs_set_initial_states")
         else:
+            if psi.dtype != _torch_c128() or not psi.is_contiguous():
+                raise ValueError("start block tensor must be contiguous complex128")
+            where = FS_DEVICE if psi.is_cuda else FS_HOST
             self._check(self.lib.fs_set_initial_states(self.h, C.c_void_p(psi.data_ptr()), psi.shape[0],
-                                                       int(damp), FS_DEVICE), "fs_set_initial_states")
+                                                       int(damp), where), "fs_set_initial_states")
 
     def solve(self, e_ref, nstates, tol=1e-6, allow_unconverged=False):
         eps = np.zeros(nstates)
@@ -236,7 +245,16 @@ class Context:
         return dict(eps=eps, resid=res, nconv=r.nconv, iters=r.iters, iters_mixed=r.iters_mixed,
                     n_hpsi=r.n_hpsi, seconds=r.seconds, status=st)
 
-    def get_states(self, n, device=False):
+    def get_states(self, n, device=False, out=None):
+        """The n states nearest E [n][npw] complex128: a numpy array, a CUDA tensor
+        (device=True), or written into `out` (a contiguous complex128 tensor, host or
+        device, e.g. pinned host memory) and returned."""
+        if out is not None:
+            if out.dtype != _torch_c128() or not out.is_contiguous() or tuple(out.shape) != (n, self.npw):
+                raise ValueError("out must be a contiguous complex128 tensor of shape (n, npw)")
+            self._check(self.lib.fs_get_states(self.h, C.c_void_p(out.data_ptr()), n,
+                                               FS_DEVICE if out.is_cuda else FS_HOST), "fs_get_states")
+            return out
         if device:
             import torch
             out = torch.empty((n, self.npw), dtype=torch.complex128, device="cuda")
