@@ -248,6 +248,22 @@ def make_batch(nbox=96, seed=1910, spacing=0.5556):
     return out
 
 
+def wavepacket_rhs(miller, L, centres, k0=0.8, s_xy=2.0, s_z=3.0) -> np.ndarray:
+    """Right-hand sides w_l of the scattering-state equation: incoming wave
+    packets w(r) = exp(-((x-x0)^2 + (y-y0)^2) / (2 s_xy^2)) exp(-(z-z0)^2 / (2 s_z^2))
+    exp(i k0 z), one per centre (x0, y0, z0), given by their analytic Fourier
+    coefficients on the plane waves with Miller indices `miller` ([npw][3],
+    G = 2 pi g / L) and normalised to unit norm.  Shape [ncentre][npw], complex128."""
+    g = np.asarray(miller, dtype=np.float64)
+    G = 2.0 * np.pi * g / np.asarray(L, dtype=np.float64)[None, :]
+    env = np.exp(-0.5 * s_xy ** 2 * (G[:, 0] ** 2 + G[:, 1] ** 2) - 0.5 * s_z ** 2 * (G[:, 2] - k0) ** 2)
+    out = []
+    for (x0, y0, z0) in centres:
+        w = env * np.exp(-1j * (G[:, 0] * x0 + G[:, 1] * y0 + (G[:, 2] - k0) * z0))
+        out.append(w / np.linalg.norm(w))
+    return np.array(out)
+
+
 def raw_start_block(nbands: int, npw: int, seed: int) -> np.ndarray:
     """Raw random start block: independent standard complex Gaussians
     (real and imaginary parts N(0,1)), shape [nbands][npw], complex128.
