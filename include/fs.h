@@ -235,6 +235,42 @@ void fs_batch_destroy(fs_batch* batch);
  * fastest (cached per grid shape for the process); *cpb receives it (may be NULL). */
 fs_status fs_autotune(fs_ctx* ctx, int* cpb);
 
+/* ---- folded-spectrum linear solve (Sec. II.C, Eq. wl1 and the M' preconditioner) ----
+ *
+ * For each right-hand side w_l, PCG minimises F = 1/2 <psi|(H - E)^2|psi> - Re<psi|w'>
+ * with w' = (H - E) w, i.e. solves (H - E)^2 psi = (H - E) w (Eq. wl1), whose solution
+ * solves the scattering-state equation (H - E) psi = w (Eq. wl) where H - E is
+ * invertible.  FP64 throughout; Polak-Ribiere directions (clamped at zero).
+ * Preconditioner: M(G) = 1/((|q|^2/2 - E)^2 + dE^2) with dE from the options, or,
+ * once eigenstates are set, the paper's
+ *   M' = M (1 - sum_i |phi_i><phi_i|) + sum_i |phi_i><phi_i| / ((eps_i - E)^2 + Delta_i^2)
+ * applied as written.  The error reported is ||(H - E) psi - w|| per right-hand side,
+ * recomputed from psi on return. */
+typedef struct {
+    int iters;                 /* PCG iterations taken (all right-hand sides step together) */
+    long long n_hpsi;          /* band applications of H */
+    double seconds;            /* wall time of the call */
+    double* err;               /* caller-allocated [nrhs], or NULL: ||(H - E) psi_l - w_l|| */
+} fs_linres;
+
+/* Eigenstates for M'.  n = 0 clears them (M alone).  phi = NULL takes the first n
+ * states of the context's last fs_solve with their eigenvalues and residuals
+ * (n <= nstates of that solve; eps and delta are ignored).  Otherwise phi holds n
+ * states [n][npw] complex128 (host or device per `where`, copied), eps[n] their
+ * eigenvalues (Ha) and delta[n] their residuals ||H phi - eps phi|| (host arrays).
+ * The states are used as given (orthonormal states are what the formula assumes). */
+fs_status fs_set_linear_states(fs_ctx* ctx, const void* phi, const double* eps, const double* delta, int n,
+                               int where);
+
+/* Solve for nrhs right-hand sides.  w and psi are [nrhs][npw] complex128, both on the
+ * host or both on the device (`where`), caller-owned; psi receives the solution and,
+ * when from_psi != 0, also holds the start guess on entry (else the start is 0).
+ * tol > 0 is the target of ||(H - E) psi - w||; maxit caps the iterations.
+ * FS_ERR_NOT_CONVERGED when some right-hand side missed tol (psi and res filled);
+ * nrhs = 0 is a no-op. */
+fs_status fs_linear_solve(fs_ctx* ctx, double e_ref, const void* w, void* psi, int nrhs, int where, int from_psi,
+                          double tol, int maxit, fs_linres* res);
+
 /* Release everything the context holds.  NULL is accepted. */
 void fs_destroy(fs_ctx* ctx);
 

@@ -50,6 +50,11 @@ class fs_result(C.Structure):
                 ("seconds", C.c_double), ("iters_mixed", C.c_int)]
 
 
+class fs_linres(C.Structure):
+    _fields_ = [("iters", C.c_int), ("n_hpsi", C.c_longlong), ("seconds", C.c_double),
+                ("err", C.POINTER(C.c_double))]
+
+
 class fs_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double),
                 ("bytes", C.c_double), ("flops", C.c_double)]
@@ -106,6 +111,10 @@ def load_library(path: str = LIB_PATH):
     lib.fs_batch_solve.restype = ip
     lib.fs_batch_destroy.argtypes = [vp]
     lib.fs_batch_destroy.restype = None
+    lib.fs_set_linear_states.argtypes = [vp, vp, dp, dp, ip, ip]
+    lib.fs_set_linear_states.restype = ip
+    lib.fs_linear_solve.argtypes = [vp, C.c_double, vp, vp, ip, ip, ip, C.c_double, ip, C.POINTER(fs_linres)]
+    lib.fs_linear_solve.restype = ip
     lib.fs_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     lib.fs_autotune.restype = ip
     lib.fs_profile.argtypes = [vp, ip]
@@ -265,6 +274,50 @@ class Context:
         self._check(self.lib.fs_get_states(self.h, out.ctypes.data_as(C.c_void_p), n, FS_HOST),
                     "fs_get_states")
         return out
+
+    # ------------------------------------------------ folded linear solve
+    def set_linear_states(self, n, phi=None, eps=None, delta=None):
+        """Eigenstates for the M' preconditioner of linear_solve: the first n states of
+        the last solve (phi None), or n given states (numpy/CPU tensor or CUDA tensor
+        [n][npw] complex128) with eigenvalues eps[n] and residuals delta[n]; n = 0 clears."""
+        if phi is None:
+            self._check(self.lib.fs_set_linear_states(self.h, None, None, None, int(n), FS_HOST),
+                        "fs_set_linear_states")
+            return
+        e = np.ascontiguousarray(eps, dtype=np.float64)
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        if isinstance(phi, np.ndarray):
+            a = np.ascontiguousarray(phi, dtype=np.complex128)
+            ptr, where = a.ctypes.data_as(C.c_void_p), FS_HOST
+        else:
+            if phi.dtype != _torch_c128() or not phi.is_contiguous():
+                raise ValueError("phi must be a contiguous complex128 tensor")
+            ptr, where = C.c_void_p(phi.data_ptr()), (FS_DEVICE if phi.is_cuda else FS_HOST)
+        self._check(self.lib.fs_set_linear_states(self.h, ptr, _dptr(e), _dptr(d), int(n), where),
+                    "fs_set_linear_states")
+
+    def linear_solve(self, w, e_ref, tol=1e-8, maxit=100000, psi=None, allow_unconverged=False):
+        """Solve (H - E)^2 psi = (H - E) w for the rows of w (numpy array: host; CUDA
+        tensor: device), starting from psi when given.  Returns (psi, info)."""
+        nrhs = int(w.shape[0])
+        err = np.zeros(max(nrhs, 1))
+        r = fs_linres()
+        r.err = _dptr(err)
+        if isinstance(w, np.ndarray):
+            wa = np.ascontiguousarray(w, dtype=np.complex128)
+            out = np.zeros_like(wa) if psi is None else np.ascontiguousarray(psi, dtype=np.complex128).copy()
+            st = self.lib.fs_linear_solve(self.h, float(e_ref), wa.ctypes.data_as(C.c_void_p),
+                                          out.ctypes.data_as(C.c_void_p), nrhs, FS_HOST, int(psi is not None),
+                                          float(tol), int(maxit), C.byref(r))
+        else:
+            import torch
+            out = torch.zeros_like(w) if psi is None else psi.clone()
+            st = self.lib.fs_linear_solve(self.h, float(e_ref), C.c_void_p(w.data_ptr()), C.c_void_p(out.data_ptr()),
+                                          nrhs, FS_DEVICE, int(psi is not None), float(tol), int(maxit),
+                                          C.byref(r))
+        if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
+            self._check(st, "fs_linear_solve")
+        return out, dict(iters=r.iters, n_hpsi=r.n_hpsi, seconds=r.seconds, err=err[:nrhs].copy(), status=st)
 
     # ------------------------------------------------ learned preconditioner
     N_PRECOND_PARAMS = 33793

@@ -272,6 +272,15 @@ struct fs_ctx {
     int init_damp = 1;
     dbuf result_states;  // double2 [nstates][npw]
     int nresult = 0;
+    std::vector<double> result_eps, result_resid;  // eigenvalues and H residuals of the last solve
+
+    // folded linear solve: eigenstates of the M' preconditioner and the PCG vectors
+    dbuf lin_phi;        // double2 [lin_n][npw]
+    int lin_n = 0;
+    std::vector<double> lin_eps, lin_delta;
+    dbuf lin_vec[9];     // psi, y, r, r_old, p, yp, ap, z, u: [nrhs][npw] each
+    dbuf lin_small;      // projections <phi_i|r_l>, coefficients, per-row scalars and partial sums
+    dbuf lin_io[2];      // device copies of host right-hand sides and solutions
 
     Prof prof;
     Mlp mlp;
@@ -299,6 +308,10 @@ template <typename T2>
 void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, const int* rowmap_in = nullptr);
 
 void ctx_prepare_fft(fs_ctx* c);
+
+// folded linear solve (fs_linear.cu): device w and psi [nrhs][npw] complex128
+fs_status linear_solve_impl(fs_ctx* c, double e_ref, const double2* w, double2* psi, int nrhs, bool from_psi,
+                            double tol, int maxit, fs_linres* res);
 
 // GEMMs (fs_gemm.cu)
 // Gram form: C(i, j) = alpha * sum_k conj(A[ia(i)][k]) * B[ib(j)][k]  (+ beta * C(i, j))

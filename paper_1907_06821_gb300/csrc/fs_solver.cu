@@ -809,6 +809,8 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
     }
     FS_CUDA(cudaStreamSynchronize(c->stream));
     c->nresult = nstates;
+    c->result_eps.assign(res->eps, res->eps + nstates);
+    c->result_resid.assign(res->resid, res->resid + nstates);
     res->nconv = nconv;
     res->iters = iters;
     res->iters_mixed = iters_mixed;

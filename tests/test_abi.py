@@ -44,6 +44,11 @@ def test_null_safe_calls_without_gpu(lib):
     assert lib.fs_last_error(None) == b"no context"
     lib.fs_create.restype = ctypes.c_int
     assert lib.fs_create(None, ctypes.c_double(1.0), None, None, None, None, None) == 1  # FS_ERR_ARG
+    lib.fs_linear_solve.restype = ctypes.c_int
+    assert lib.fs_linear_solve(None, ctypes.c_double(0.0), None, None, 0, 0, 0, ctypes.c_double(1e-8), 10,
+                               None) == 1
+    lib.fs_set_linear_states.restype = ctypes.c_int
+    assert lib.fs_set_linear_states(None, None, None, None, 0, 0) == 1
 
 
 def test_binding_structs_match_header():
@@ -56,5 +61,5 @@ def test_binding_structs_match_header():
         body = re.sub(r"/\*.*?\*/", "", blocks[struct], flags=re.S)
         return re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[\d+\])?\s*;", body)
     for cls, name in ((fs.fs_grid, "fs_grid"), (fs.fs_projectors, "fs_projectors"),
-                      (fs.fs_options, "fs_options"), (fs.fs_result, "fs_result")):
+                      (fs.fs_options, "fs_options"), (fs.fs_result, "fs_result"), (fs.fs_linres, "fs_linres")):
         assert [f[0] for f in cls._fields_] == fields(name), name
