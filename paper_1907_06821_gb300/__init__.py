@@ -111,7 +111,7 @@ def load_library(path: str = LIB_PATH):
     lib.fs_batch_solve.restype = ip
     lib.fs_batch_destroy.argtypes = [vp]
     lib.fs_batch_destroy.restype = None
-    lib.fs_set_linear_states.argtypes = [vp, vp, dp, dp, ip, ip]
+    lib.fs_set_linear_states.argtypes = [vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), ip, ip]
     lib.fs_set_linear_states.restype = ip
     lib.fs_linear_solve.argtypes = [vp, C.c_double, vp, vp, ip, ip, ip, C.c_double, ip, C.POINTER(fs_linres)]
     lib.fs_linear_solve.restype = ip
