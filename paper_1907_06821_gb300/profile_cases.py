@@ -3,6 +3,7 @@
     python -m paper_1907_06821_gb300.profile_cases apply --workload wire --bands 64 --precision mixed
     python -m paper_1907_06821_gb300.profile_cases solve --workload wire --maxit 20
     python -m paper_1907_06821_gb300.profile_cases apply --workload medium --bands 64
+    python -m paper_1907_06821_gb300.profile_cases linear --workload medium --nrhs 4 --states 128 --maxit 3000
 
 ``medium`` is a 24 x 24 x 48 bohr box on a 48 x 48 x 96 grid at 20 Ry (41,657
 plane waves) with 64 wells and 8 projectors per atom: operands larger than the
@@ -32,6 +33,34 @@ def _print_stats(ctx):
                   f"TF/s={v['flops'] / max(v['ms'], 1e-9) / 1e9:8.2f} GB/s={v['bytes'] / max(v['ms'], 1e-9) / 1e6:9.1f}")
 
 
+def _linear(a, w, ctx, fs, fi, np):
+    """The folded linear solve of nrhs wave packets with M alone, then with M' from
+    the `states` eigenpairs nearest E found by the mixed-precision eigensolve (a
+    separate FP64-checked solve); one JSON line with iterations, times and errors."""
+    import json
+    import time
+    L = np.asarray(w.L)
+    cen = [(L[0] * (0.3 + 0.4 * i / max(a.nrhs - 1, 1)), L[1] * 0.5, L[2] * (0.2 + 0.6 * i / max(a.nrhs - 1, 1)))
+           for i in range(a.nrhs)]
+    W = fi.wavepacket_rhs(ctx.gvectors(), L, cen)
+    out = {"workload": a.workload, "npw": ctx.npw, "nrhs": a.nrhs, "tol": a.tol, "e_ref": w.e_ref}
+    _, r0 = ctx.linear_solve(W, w.e_ref, tol=a.tol, maxit=a.maxit, allow_unconverged=True)
+    out["M"] = {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in r0.items()}
+    es = fs.Context.from_workload(w, precision=fs.FS_MIXED, maxit=3000)
+    es.set_initial_states(fi.raw_start_block(a.states + max(4, a.states // 16), es.npw, 17), damp=True)
+    t0 = time.time()
+    r = es.solve(w.e_ref, a.states, tol=1e-6, allow_unconverged=True)
+    t_eig = time.time() - t0
+    phi = es.get_states(a.states)
+    es.close()
+    ctx.set_linear_states(a.states, phi=phi, eps=r["eps"], delta=r["resid"])
+    _, r1 = ctx.linear_solve(W, w.e_ref, tol=a.tol, maxit=a.maxit, allow_unconverged=True)
+    out["eigensolve"] = {"states": a.states, "nconv": r["nconv"], "seconds": t_eig,
+                         "max_resid": float(np.max(r["resid"]))}
+    out["M_prime"] = {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in r1.items()}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     import numpy as np
     import torch
@@ -40,13 +69,16 @@ def main(argv=None):
     import paper_1907_06821_gb300 as fs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["apply", "solve"])
+    ap.add_argument("case", choices=["apply", "solve", "linear"])
     ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "medium"])
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--maxit", type=int, default=20)
     ap.add_argument("--verbose", action="store_true", help="per-iteration solver log on stderr")
+    ap.add_argument("--nrhs", type=int, default=4, help="linear: right-hand sides (wave packets)")
+    ap.add_argument("--states", type=int, default=128, help="linear: eigenstates nearest E for M'")
+    ap.add_argument("--tol", type=float, default=1e-8, help="linear: target of ||(H - E) psi - w||")
     a = ap.parse_args(argv)
     if a.workload == "medium":
         w = fi.make_box(L=(24.0, 24.0, 48.0), n=(48, 48, 96), ecut=10.0, natom=64, widths=(0.8, 1.2),
@@ -63,6 +95,10 @@ def main(argv=None):
                 ctx.profile(True)
             ctx.apply_H(X, shift=w.e_ref)
         torch.cuda.synchronize()
+    elif a.case == "linear":
+        _linear(a, w, ctx, fs, fi, np)
+        ctx.close()
+        return
     else:
         ctx.set_initial_states(fi.raw_start_block(w.nbands, ctx.npw, 17), damp=True)
         ctx.profile(True)
