@@ -271,6 +271,34 @@ fs_status fs_set_linear_states(fs_ctx* ctx, const void* phi, const double* eps, 
 fs_status fs_linear_solve(fs_ctx* ctx, double e_ref, const void* w, void* psi, int nrhs, int where, int from_psi,
                           double tol, int maxit, fs_linres* res);
 
+/* ---- Chebyshev filter diagonalisation (Sec. II.C, the ChebFD producer of the states near E) ----
+ *
+ * A block of nvec seeded random vectors is filtered by p(Hs) = sum_n g_n mu_n T_n(Hs),
+ * Hs = (H - c)/e mapping [emin, emax] to [-1, 1], mu_n the Chebyshev coefficients of the
+ * indicator of the window [E - half_width, E + half_width] and g_n the Jackson damping
+ * for the given degree (T_n by the three-term recurrence, one H application per degree),
+ * then a Rayleigh-Ritz step of H on the filtered block gives the block of the next step;
+ * `steps` steps in all, FP64.  [emin, emax] must contain the spectrum of H
+ * (fs_spectral_bounds gives an estimate).  The pairs inside the window, ordered by
+ * (|eps - E|, eps), at most nwant of them, become the context's result: their states
+ * are read with fs_get_states and serve fs_set_linear_states(phi = NULL).  Pairs with a
+ * large residual ("ghost states") can appear; their residuals say so. */
+typedef struct {
+    int nfound;                /* pairs reported (inside the window, at most nwant) */
+    long long n_hpsi;          /* band applications of H */
+    double seconds;            /* wall time of the call */
+    double* eps;               /* caller-allocated [nwant]: eigenvalues, Ha */
+    double* resid;             /* caller-allocated [nwant]: ||H phi - eps phi|| */
+} fs_chebfd_result;
+
+fs_status fs_chebfd(fs_ctx* ctx, double e_ref, double half_width, double emin, double emax, int degree, int nvec,
+                    int steps, unsigned long long seed, int nwant, fs_chebfd_result* res);
+
+/* Estimated spectral bounds of H: iters (>= 2) Lanczos steps on one seeded vector; the
+ * extreme eigenvalues of the tridiagonal matrix widened by the norm of the last
+ * residual vector. */
+fs_status fs_spectral_bounds(fs_ctx* ctx, int iters, double* emin, double* emax);
+
 /* Release everything the context holds.  NULL is accepted. */
 void fs_destroy(fs_ctx* ctx);
 

@@ -55,6 +55,11 @@ class fs_linres(C.Structure):
                 ("err", C.POINTER(C.c_double))]
 
 
+class fs_chebfd_result(C.Structure):
+    _fields_ = [("nfound", C.c_int), ("n_hpsi", C.c_longlong), ("seconds", C.c_double),
+                ("eps", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double))]
+
+
 class fs_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_longlong), ("ms", C.c_double),
                 ("bytes", C.c_double), ("flops", C.c_double)]
@@ -115,6 +120,11 @@ def load_library(path: str = LIB_PATH):
     lib.fs_set_linear_states.restype = ip
     lib.fs_linear_solve.argtypes = [vp, C.c_double, vp, vp, ip, ip, ip, C.c_double, ip, C.POINTER(fs_linres)]
     lib.fs_linear_solve.restype = ip
+    lib.fs_chebfd.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, ip, ip, ip, C.c_ulonglong, ip,
+                              C.POINTER(fs_chebfd_result)]
+    lib.fs_chebfd.restype = ip
+    lib.fs_spectral_bounds.argtypes = [vp, ip, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    lib.fs_spectral_bounds.restype = ip
     lib.fs_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     lib.fs_autotune.restype = ip
     lib.fs_profile.argtypes = [vp, ip]
@@ -318,6 +328,27 @@ class Context:
         if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
             self._check(st, "fs_linear_solve")
         return out, dict(iters=r.iters, n_hpsi=r.n_hpsi, seconds=r.seconds, err=err[:nrhs].copy(), status=st)
+
+    # ------------------------------------------------ ChebFD
+    def spectral_bounds(self, iters=40):
+        """(emin, emax) estimated by Lanczos steps widened by the last residual norm."""
+        lo, hi = C.c_double(), C.c_double()
+        self._check(self.lib.fs_spectral_bounds(self.h, int(iters), C.byref(lo), C.byref(hi)), "fs_spectral_bounds")
+        return lo.value, hi.value
+
+    def chebfd(self, e_ref, half_width, emin, emax, degree, nvec, steps, seed=1, nwant=None):
+        """Chebyshev filter diagonalisation; returns dict(eps, resid, nfound, n_hpsi, seconds)
+        for the pairs inside the window (states via get_states)."""
+        nwant = nvec if nwant is None else int(nwant)
+        eps = np.zeros(max(nwant, 1))
+        res = np.zeros(max(nwant, 1))
+        r = fs_chebfd_result()
+        r.eps = _dptr(eps)
+        r.resid = _dptr(res)
+        self._check(self.lib.fs_chebfd(self.h, float(e_ref), float(half_width), float(emin), float(emax), int(degree),
+                                       int(nvec), int(steps), int(seed), nwant, C.byref(r)), "fs_chebfd")
+        n = r.nfound
+        return dict(eps=eps[:n].copy(), resid=res[:n].copy(), nfound=n, n_hpsi=r.n_hpsi, seconds=r.seconds)
 
     # ------------------------------------------------ learned preconditioner
     N_PRECOND_PARAMS = 33793

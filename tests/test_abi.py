@@ -49,6 +49,8 @@ def test_null_safe_calls_without_gpu(lib):
                                None) == 1
     lib.fs_set_linear_states.restype = ctypes.c_int
     assert lib.fs_set_linear_states(None, None, None, None, 0, 0) == 1
+    lib.fs_spectral_bounds.restype = ctypes.c_int
+    assert lib.fs_spectral_bounds(None, 10, None, None) == 1
 
 
 def test_binding_structs_match_header():
@@ -61,5 +63,6 @@ def test_binding_structs_match_header():
         body = re.sub(r"/\*.*?\*/", "", blocks[struct], flags=re.S)
         return re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*(?:\[\d+\])?\s*;", body)
     for cls, name in ((fs.fs_grid, "fs_grid"), (fs.fs_projectors, "fs_projectors"),
-                      (fs.fs_options, "fs_options"), (fs.fs_result, "fs_result"), (fs.fs_linres, "fs_linres")):
+                      (fs.fs_options, "fs_options"), (fs.fs_result, "fs_result"), (fs.fs_linres, "fs_linres"),
+                      (fs.fs_chebfd_result, "fs_chebfd_result")):
         assert [f[0] for f in cls._fields_] == fields(name), name
