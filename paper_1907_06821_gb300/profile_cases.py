@@ -61,6 +61,28 @@ def _linear(a, w, ctx, fs, fi, np):
     print(json.dumps(out), flush=True)
 
 
+def _chebfd(a, w, ctx, fi, np):
+    """ChebFD states near E (Lanczos bounds, window filter, Rayleigh-Ritz), then the
+    folded linear solve of nrhs wave packets with M' built from them; one JSON line."""
+    import json
+    lo, hi = ctx.spectral_bounds(40)
+    r = ctx.chebfd(w.e_ref, a.halfwidth, lo, hi, a.degree, a.nvec, a.steps, seed=9)
+    res = r["resid"]
+    out = {"workload": a.workload, "npw": ctx.npw, "bounds": [lo, hi], "window": [w.e_ref - a.halfwidth,
+           w.e_ref + a.halfwidth], "degree": a.degree, "nvec": a.nvec, "steps": a.steps,
+           "chebfd": {"nfound": r["nfound"], "seconds": r["seconds"], "n_hpsi": r["n_hpsi"],
+                      "resid_le_1e-6": int(np.sum(res <= 1e-6)), "resid_le_1e-8": int(np.sum(res <= 1e-8)),
+                      "resid_median": float(np.median(res)) if len(res) else None}}
+    L = np.asarray(w.L)
+    cen = [(L[0] * (0.3 + 0.4 * i / max(a.nrhs - 1, 1)), L[1] * 0.5, L[2] * (0.2 + 0.6 * i / max(a.nrhs - 1, 1)))
+           for i in range(a.nrhs)]
+    W = fi.wavepacket_rhs(ctx.gvectors(), L, cen)
+    ctx.set_linear_states(r["nfound"])
+    _, rl = ctx.linear_solve(W, w.e_ref, tol=a.tol, maxit=a.maxit, allow_unconverged=True)
+    out["linear_M_prime_from_chebfd"] = {k: (v.tolist() if hasattr(v, "tolist") else v) for k, v in rl.items()}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     import numpy as np
     import torch
@@ -69,7 +91,7 @@ def main(argv=None):
     import paper_1907_06821_gb300 as fs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["apply", "solve", "linear"])
+    ap.add_argument("case", choices=["apply", "solve", "linear", "chebfd"])
     ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "medium"])
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -79,6 +101,10 @@ def main(argv=None):
     ap.add_argument("--nrhs", type=int, default=4, help="linear: right-hand sides (wave packets)")
     ap.add_argument("--states", type=int, default=128, help="linear: eigenstates nearest E for M'")
     ap.add_argument("--tol", type=float, default=1e-8, help="linear: target of ||(H - E) psi - w||")
+    ap.add_argument("--nvec", type=int, default=96, help="chebfd: block size")
+    ap.add_argument("--degree", type=int, default=300, help="chebfd: filter degree")
+    ap.add_argument("--steps", type=int, default=3, help="chebfd: filter steps")
+    ap.add_argument("--halfwidth", type=float, default=0.04, help="chebfd: window half-width, Ha")
     a = ap.parse_args(argv)
     if a.workload == "medium":
         w = fi.make_box(L=(24.0, 24.0, 48.0), n=(48, 48, 96), ecut=10.0, natom=64, widths=(0.8, 1.2),
@@ -97,6 +123,10 @@ def main(argv=None):
         torch.cuda.synchronize()
     elif a.case == "linear":
         _linear(a, w, ctx, fs, fi, np)
+        ctx.close()
+        return
+    elif a.case == "chebfd":
+        _chebfd(a, w, ctx, fi, np)
         ctx.close()
         return
     else:
