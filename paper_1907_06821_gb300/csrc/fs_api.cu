@@ -227,7 +227,6 @@ fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const d
         if (c->opt.gemm_path != FS_GEMM_TENSOR && c->opt.gemm_path != FS_GEMM_CUDA_CORES)
             throw fs_error(FS_ERR_ARG, "bad gemm_path");
         c->gemm_path = c->opt.gemm_path;
-        if (const char* e = std::getenv("FS_TC_GRAM_KCHUNK")) c->tc_gram_kchunk = std::max(16, std::atoi(e));
         c->errflag.alloc(sizeof(int));
         FS_CUDA(cudaMemset(c->errflag.p, 0, sizeof(int)));
         if (c->opt.cuda_stream) {

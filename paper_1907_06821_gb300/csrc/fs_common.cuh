@@ -287,7 +287,6 @@ struct fs_ctx {
     SolverMem smem;
     dbuf errflag;     // int: set by a device-side wait that gave up
     int gemm_path = 0;
-    int tc_gram_kchunk = 1 << 30;  // complex k per tensor-memory accumulation (Gram form)
     std::string err;
 };
 

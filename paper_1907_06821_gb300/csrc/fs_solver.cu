@@ -44,7 +44,6 @@ template <typename T2> struct Blocks {
         for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->ensure(b);
         haveP = false;
     }
-    void free_all() {}
 };
 
 void swapb(dbuf& a, dbuf& b) {
