@@ -299,6 +299,12 @@ fs_status fs_chebfd(fs_ctx* ctx, double e_ref, double half_width, double emin, d
  * residual vector. */
 fs_status fs_spectral_bounds(fs_ctx* ctx, int iters, double* emin, double* emax);
 
+/* Failure-path check without a GPU fault: runs the library's bounded device wait (the one
+ * the tensor-core pipelines use) on a barrier that nothing completes, polling `polls`
+ * times (1 .. 2^24); the wait gives up, raises the context's error flag, and the call
+ * returns FS_ERR_TIMEOUT as a pipeline timeout would.  The context stays usable. */
+fs_status fs_wait_selftest(fs_ctx* ctx, long long polls);
+
 /* Release everything the context holds.  NULL is accepted. */
 void fs_destroy(fs_ctx* ctx);
 

@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH):
     lib.fs_chebfd.restype = ip
     lib.fs_spectral_bounds.argtypes = [vp, ip, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.fs_spectral_bounds.restype = ip
+    lib.fs_wait_selftest.argtypes = [vp, C.c_longlong]
+    lib.fs_wait_selftest.restype = ip
     lib.fs_autotune.argtypes = [vp, C.POINTER(C.c_int)]
     lib.fs_autotune.restype = ip
     lib.fs_profile.argtypes = [vp, ip]
@@ -328,6 +330,11 @@ class Context:
         if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
             self._check(st, "fs_linear_solve")
         return out, dict(iters=r.iters, n_hpsi=r.n_hpsi, seconds=r.seconds, err=err[:nrhs].copy(), status=st)
+
+    def wait_selftest(self, polls=4096):
+        """Run the bounded device wait on a barrier nothing completes; raises FSError
+        with FS_ERR_TIMEOUT (the failure path of the tensor-core pipelines)."""
+        self._check(self.lib.fs_wait_selftest(self.h, int(polls)), "fs_wait_selftest")
 
     # ------------------------------------------------ ChebFD
     def spectral_bounds(self, iters=40):

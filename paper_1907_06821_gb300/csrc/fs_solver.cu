@@ -417,6 +417,18 @@ struct Solver {
         double2* GB = s.GB.as<double2>();
         gemm_gram<T2>(c, m, m, c->npw, Y, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
         gemm_gram<T2>(c, m, m, c->npw, X, c->npw, nullptr, X, c->npw, nullptr, GB, 1, m, 1.0, 0.0);
+        {
+            // a non-finite start block (or H image) is reported before a dense eigensolve sees it:
+            // the diagonals of G_B and G_A are the squared norms of the bands and of their images
+            std::vector<double2> dg(2 * (size_t)m);
+            FS_CUDA(cudaMemcpy2DAsync(dg.data(), sizeof(double2), GB, (m + 1) * sizeof(double2), sizeof(double2), m,
+                                      cudaMemcpyDeviceToHost, c->stream));
+            FS_CUDA(cudaMemcpy2DAsync(dg.data() + m, sizeof(double2), GA, (m + 1) * sizeof(double2), sizeof(double2),
+                                      m, cudaMemcpyDeviceToHost, c->stream));
+            FS_CUDA(cudaStreamSynchronize(c->stream));
+            for (const double2& v : dg)
+                if (!std::isfinite(v.x)) throw fs_error(FS_ERR_NUMERIC, "non-finite values in the block or its H image");
+        }
         int info = rr_basis(m, true, tau_for<T2>(), piv_for<T2>());
         if (info != 0) throw fs_error(FS_ERR_NUMERIC, "start block is rank deficient (info " + std::to_string(info) + ")");
         rotate_simple(B, m);

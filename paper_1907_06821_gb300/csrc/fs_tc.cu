@@ -513,6 +513,33 @@ tcq_gram_kernel(int M, int N, int TJ, int nkbl, int kbs, const unsigned char* __
     tcq_teardown(t, ok, errflag);
 }
 
+// The bounded wait of the pipelines, on a barrier that nothing completes: it
+// polls `limit` times, gives up and raises the context's error flag.
+__global__ void wait_selftest_kernel(long long limit, int* errflag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init_n(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t a = smem_u32(&bar);
+        bool ok = false;
+        for (long long it = 0; it < limit && !ok; ++it) {
+            uint32_t r;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(r)
+                : "r"(a), "r"(0u)
+                : "memory");
+            ok = r != 0;
+        }
+        if (!ok) atomicExch(errflag, 1);
+    }
+}
+
 std::once_flag g_attr_once;
 void set_attrs_once() {
     cudaFuncSetAttribute((const void*)tcq_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QSMEM);
@@ -650,3 +677,21 @@ template void tc_gemm_nn<double2>(fs_ctx*, int, int, int, const double2*, long, 
                                   float2*, long, const int*, double, double, const float2*, long, int);
 template void tc_gemm_nn<float2>(fs_ctx*, int, int, int, const float2*, long, long, const float2*, long, const int*,
                                  float2*, long, const int*, double, double, const float2*, long, int);
+
+extern "C" fs_status fs_wait_selftest(fs_ctx* c, long long polls) {
+    if (!c) return FS_ERR_ARG;
+    if (polls < 1 || polls > (1ll << 24)) {
+        c->err = "fs_wait_selftest: polls out of range [1, 2^24]";
+        return FS_ERR_ARG;
+    }
+    try {
+        wait_selftest_kernel<<<1, 32, 0, c->stream>>>(polls, ctx_errflag(c));
+        FS_CUDA(cudaGetLastError());
+        ctx_check_errflag(c);
+        c->err.clear();
+        return FS_OK;
+    } catch (const fs_error& e) {
+        c->err = e.msg;
+        return e.code;
+    }
+}

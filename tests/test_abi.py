@@ -51,6 +51,8 @@ def test_null_safe_calls_without_gpu(lib):
     assert lib.fs_set_linear_states(None, None, None, None, 0, 0) == 1
     lib.fs_spectral_bounds.restype = ctypes.c_int
     assert lib.fs_spectral_bounds(None, 10, None, None) == 1
+    lib.fs_wait_selftest.restype = ctypes.c_int
+    assert lib.fs_wait_selftest(None, ctypes.c_longlong(10)) == 1
 
 
 def test_binding_structs_match_header():
