@@ -140,7 +140,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["seconds_per_solve"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {res['desc']}", "sample": res["sample"]},
+            "config": {"workload": res["desc"], "precision": "fp64 (oracle)", "tol": TOL, "sample": res["sample"]},
             "cpu_baseline": {"value": res["value"], "unit": "states/s", "cores": res["cores"],
                              "kind": "oracle", "sample": res["sample"]},
             "e2e": {"value": res["value"], "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -181,8 +181,13 @@ def cpu_baseline(name, gpu_counts):
     value = w.nstates / est
     sample = (f"oracle H on {nb} bands ({t_h * 1e3:.1f} ms/band) and one {m}x{m} Gram product over "
               f"{h.npw} plane waves ({t_gram:.2f} s), {how}; setup {t_setup:.1f} s")
-    return dict(value=value, cores=cores, sample=sample, seconds_per_solve=est,
-                desc=f"grid {w.n}, {h.npw} PWs, {w.natom} atoms, {w.nproj} proj/atom, {w.nstates} states")
+    return dict(value=value, cores=cores, sample=sample, seconds_per_solve=est, desc=workload_desc(name, w, h.npw))
+
+
+def workload_desc(name, w, npw):
+    """The workload string both arms report in config.workload."""
+    return (f"{name}: grid {tuple(w.n)}, {npw} PWs, {w.natom} atoms, {w.nproj} proj/atom, "
+            f"{w.nstates} states nearest E_ref={w.e_ref:.6f} Ha")
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -309,8 +314,7 @@ def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, cloc
         "metric": METRIC, "value": nconv / tmax, "unit": "states/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tmax * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: grid {tuple(w.n)}, {ctx.npw} PWs, {w.natom} atoms, "
-                               f"{w.nproj} proj/atom, {w.nstates} states nearest E_ref={w.e_ref:.6f} Ha",
+        "config": {"workload": workload_desc(args.workload, w, ctx.npw),
                    "precision": args.precision, "tol": TOL, "l2": "inputs larger than L2 (each band block "
                    f"{w.nbands * ctx.npw * (8 if fp32 else 16) / 1e6:.0f} MB)", "start_block_seed": 17},
         "roofline": roof,
