@@ -100,3 +100,29 @@ def test_eigenstate_preconditioner_accelerates_pcg():
     assert np.all(err_m <= 1e-8) and np.all(err_p <= 1e-8)
     assert it_p < it_m
     assert np.linalg.norm(psi_p - psi_m) <= 1e-6 * np.linalg.norm(psi_m)
+
+
+def test_wavepacket_coefficients_are_the_fourier_transform_of_the_packet():
+    """The analytic plane-wave coefficients of the wave-packet right-hand side
+    equal the FFT of the periodised packet sampled on the grid (Poisson
+    summation; the grid is fine enough that aliasing and the sphere cut-off
+    are negligible)."""
+    w = fi.make_box(L=(12.0, 12.0, 24.0), n=(48, 48, 96), ecut=60.0, natom=1, widths=(), nstates=1, e_ref=0.0,
+                    seed=0)
+    g, _ = pw.sphere(w.L, w.n, w.ecut, w.k)
+    x0, y0, z0, k0, sxy, sz = 6.0, 5.0, 11.0, 0.8, 1.2, 1.8
+    W = fi.wavepacket_rhs(g, w.L, [(x0, y0, z0)], k0=k0, s_xy=sxy, s_z=sz)[0]
+    n = np.asarray(w.n)
+    r = [np.arange(n[d]) * w.L[d] / n[d] for d in range(3)]
+    X, Y, Z = np.meshgrid(*r, indexing="ij")
+    f = np.zeros(X.shape, dtype=np.complex128)
+    for a in (-1, 0, 1):                                 # the images that reach the cell
+        for b in (-1, 0, 1):
+            for d in (-1, 0, 1):
+                Xs, Ys, Zs = X + a * w.L[0], Y + b * w.L[1], Z + d * w.L[2]
+                f += np.exp(-((Xs - x0) ** 2 + (Ys - y0) ** 2) / (2 * sxy ** 2) - (Zs - z0) ** 2 / (2 * sz ** 2)
+                            + 1j * k0 * Zs)
+    F = np.fft.fftn(f)                                   # sum_j f(r_j) e^{-i G.r_j}
+    c = F[tuple((g % n[None, :]).T)]
+    c = c / np.linalg.norm(c)
+    assert np.abs(c - W).max() <= 1e-10
