@@ -690,7 +690,7 @@ struct Solver {
                 for (int i = 0; i < nstates; ++i) lg += std::log(std::max(ra[i] / tol_a(th[i], target), 1.0));
                 double metric = std::exp(lg / nstates);
                 if (hworst >= 0) metric = hworst / target;
-                else if (best < 1e299 && it % 5 != 0) metric = best;  // judge on the H check when it runs
+                else if (best < 1e299 && it % 5 != 0) metric = best;  // decided by the H check when it runs
                 if (metric < 0.7 * best) {
                     best = metric;
                     since_best = 0;
