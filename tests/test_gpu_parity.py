@@ -159,3 +159,26 @@ def test_wire_apply_H_sampled_bands(fs):
         out32 = c.apply_H(torch.from_numpy(X.astype(np.complex64)).cuda(), shift=0.1).cpu().numpy()
     assert rel_err(out64[pick], ref) < 1e-12
     assert rel_err(out32[pick].astype(np.complex128), ref) < tol32(w)
+
+
+def test_wire_solve_sampled_states(fs):
+    """Full-size wire solve in the benchmark's configuration (mixed precision,
+    the 256 states nearest E_ref, start block seed 17): every state passes the
+    library's FP64 check; eight states (first, last, the largest reported
+    residual and five between) are re-checked by the oracle's FP64 H: residual
+    <= 1e-6 and equal to the reported one, orthonormal."""
+    w = fi.make_config("wire")
+    with make_ctx(fs, w, precision=fs.FS_MIXED) as c:
+        c.set_initial_states(fi.raw_start_block(w.nbands, c.npw, 17), damp=True)
+        r = c.solve(w.e_ref, w.nstates, tol=TOL_RES)
+        states = c.get_states(w.nstates)
+    assert r["nconv"] == w.nstates
+    d = np.abs(r["eps"] - w.e_ref)
+    assert np.all(np.diff(d) >= -1e-12)
+    pick = sorted({0, w.nstates - 1, int(np.argmax(r["resid"]))} | set(np.linspace(16, 240, 5).astype(int).tolist()))
+    h = pw.Hamiltonian(w)
+    X = states[pick]
+    res = np.linalg.norm(h.apply(X) - r["eps"][pick][:, None] * X, axis=1)
+    assert res.max() <= TOL_RES
+    assert np.allclose(res, r["resid"][pick], rtol=0, atol=1e-9)
+    assert np.abs(X.conj() @ X.T - np.eye(len(pick))).max() < 1e-10
