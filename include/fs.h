@@ -159,11 +159,16 @@ fs_status fs_set_initial_states(fs_ctx* ctx, const void* psi, int n, int damp, i
 
 /* Solve for the nstates eigenpairs nearest e_ref to residual tol (Ha).
  * res->eps and res->resid must hold nstates doubles.  Returns
- * FS_ERR_NOT_CONVERGED (results filled) when the cap is reached. */
+ * FS_ERR_NOT_CONVERGED (results filled) when the cap is reached;
+ * FS_ERR_NUMERIC when the block or its H image is not finite (a non-finite
+ * start block is caught before any dense eigensolve) or the basis selection
+ * fails; FS_ERR_TIMEOUT when a bounded device wait gave up.  The context
+ * stays usable after any of these. */
 fs_status fs_solve(fs_ctx* ctx, double e_ref, int nstates, double tol, fs_result* res);
 
-/* Copy the n first states of the last solve (in the order of res->eps),
- * [n][npw] complex128, to host or device memory. */
+/* Copy the n first states of the last solve (in the order of res->eps), or of
+ * the last fs_chebfd (in the order of its eps), [n][npw] complex128, to host or
+ * device memory. */
 fs_status fs_get_states(fs_ctx* ctx, void* psi, int n, int where);
 
 /* Per-kernel-class timing.  fs_profile(ctx, 1) resets the counters and
@@ -173,7 +178,9 @@ fs_status fs_get_states(fs_ctx* ctx, void* psi, int n, int where);
  * class name (static string), launches, summed event time (ms), and the
  * algorithmic bytes and flops of those launches (the minimum traffic the
  * kernel's function implies: each operand read once, each result written
- * once).  *count receives the number of classes. */
+ * once).  FP64 work (the FP64 stage, the FP64 check of an FP32 result, the
+ * linear solve, ChebFD) is counted in its own classes, named with "_fp64".
+ * *count receives the number of classes. */
 typedef struct {
     const char* name;
     long long launches;
