@@ -144,9 +144,11 @@ fs_status fs_apply_H(fs_ctx* ctx, const void* psi, void* hpsi, int nband,
  *     nothing needs clearing, but calls that overlap on the GPU (two streams,
  *     two threads) race on it: serialise them.
  *   - The first call on a device looks up the array's device address with
- *     cudaGetSymbolAddress (with that device current); make that first call
- *     before any stream capture.  Each GPU that loads the library holds the
- *     64 MiB until the process exits.
+ *     cudaGetSymbolAddress; the context's device (the one current at
+ *     fs_create) must be the current device, else FS_ERR_ARG.  Each GPU that
+ *     loads the library holds the 64 MiB until the process exits.
+ *   - The call ends by synchronising the context's stream, so it must not be
+ *     made while that stream is being captured into a CUDA graph.
  *   - The context itself (fs_create) still allocates; create it beforehand. */
 fs_status fs_apply_H_static(fs_ctx* ctx, const void* psi, void* hpsi, int nband, double shift);
 
@@ -221,6 +223,20 @@ fs_status fs_precond_eval(fs_ctx* ctx, const float* features, int rows, float* z
  * (DEVICE grad[33,793]) with respect to the parameters; DEVICE inputs */
 fs_status fs_precond_loss_grad(fs_ctx* ctx, const float* features, const float* target, const float* weight,
                                int rows, float* loss, float* grad);
+/* Features and training labels of given residual rows, by the device steps a
+ * recording solve of fs_precond_train takes (for checking them against a
+ * reference implementation).  nb residual rows R, their bands X and nref
+ * reference states Xref are DEVICE arrays [..][npw], complex128 (precision
+ * FS_FP64) or complex64 (FS_MIXED); d is a HOST array [nb] of the distances
+ * d_i = <x_i, (H - E) x_i> (Ha).  The correction of band i is
+ * e_i = Xref Xref^H x_i - x_i; with it, per (band i, shell s), the label is
+ * log max(Re<M R_i, e_i>_s / ||M R_i||_s^2, 1e-3) minus its weighted mean over s
+ * and the weight the shell's share of ||M R_i||^2, M = M(G) at e_ref.  Shells:
+ * 32 uniform bins of |q|^2/2 over [0, ecut].  Outputs are DEVICE float arrays:
+ * F [nb * 32][4] (row i * 32 + s), zt and wt [nb * 32].  X = NULL computes the
+ * features only (Xref, zt, wt ignored). */
+fs_status fs_precond_features(fs_ctx* ctx, double e_ref, const void* R, const void* X, const void* Xref, int nref,
+                              const double* d, int nb, int precision, float* F, float* zt, float* wt);
 
 /* Batched independent boxes (the fragment setting of the paper's LS3DF step,
  * Sec. II.B: many small problems of uneven size solved independently).  A

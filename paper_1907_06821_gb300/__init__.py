@@ -110,6 +110,8 @@ def load_library(path: str = LIB_PATH):
     lib.fs_precond_eval.restype = ip
     lib.fs_precond_loss_grad.argtypes = [vp, vp, vp, vp, ip, C.POINTER(C.c_float), vp]
     lib.fs_precond_loss_grad.restype = ip
+    lib.fs_precond_features.argtypes = [vp, dp, vp, vp, vp, ip, C.POINTER(C.c_double), ip, ip, vp, vp, vp]
+    lib.fs_precond_features.restype = ip
     lib.fs_batch_create.argtypes = [ip, C.POINTER(vp), ip, C.POINTER(vp)]
     lib.fs_batch_create.restype = ip
     lib.fs_batch_solve.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int), dp, vp, C.POINTER(C.c_int)]
@@ -359,6 +361,7 @@ class Context:
 
     # ------------------------------------------------ learned preconditioner
     N_PRECOND_PARAMS = 33793
+    N_SHELL = 32
 
     def precond_train(self, e_ref, nstates, tol=1e-6, epochs=200, lr=1e-3):
         """Train the learned G-shell preconditioner from this context's own solves; returns the loss."""
@@ -397,6 +400,24 @@ class Context:
                                                   features.shape[0], C.byref(loss), C.c_void_p(g.data_ptr())),
                     "fs_precond_loss_grad")
         return float(loss.value), g
+
+    def precond_features(self, e_ref, R, d, X=None, Xref=None):
+        """Features [nb*32][4] (and labels, weights [nb*32] when X and Xref are given) of the
+        residual rows R (CUDA complex128 or complex64 tensors [nb][npw]; d: host distances)."""
+        import torch
+        nb = R.shape[0]
+        prec = FS_FP64 if R.dtype == torch.complex128 else FS_MIXED
+        F = torch.empty((nb * self.N_SHELL, 4), dtype=torch.float32, device=R.device)
+        zt = torch.empty(nb * self.N_SHELL, dtype=torch.float32, device=R.device)
+        wt = torch.empty(nb * self.N_SHELL, dtype=torch.float32, device=R.device)
+        dd = np.ascontiguousarray(d, dtype=np.float64)
+        lab = X is not None
+        self._check(self.lib.fs_precond_features(
+            self.h, float(e_ref), C.c_void_p(R.data_ptr()), C.c_void_p(X.data_ptr() if lab else None),
+            C.c_void_p(Xref.data_ptr() if lab else None), Xref.shape[0] if lab else 0, _dptr(dd), nb, prec,
+            C.c_void_p(F.data_ptr()), C.c_void_p(zt.data_ptr()), C.c_void_p(wt.data_ptr())),
+            "fs_precond_features")
+        return (F, zt, wt) if lab else F
 
     def autotune(self):
         """Pick the FFT column tile for this grid by timing; returns columns per block."""

@@ -227,6 +227,7 @@ fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const d
         if (c->opt.gemm_path != FS_GEMM_TENSOR && c->opt.gemm_path != FS_GEMM_CUDA_CORES)
             throw fs_error(FS_ERR_ARG, "bad gemm_path");
         c->gemm_path = c->opt.gemm_path;
+        FS_CUDA(cudaGetDevice(&c->device));
         c->errflag.alloc(sizeof(int));
         FS_CUDA(cudaMemset(c->errflag.p, 0, sizeof(int)));
         if (c->opt.cuda_stream) {

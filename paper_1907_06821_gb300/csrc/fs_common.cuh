@@ -232,6 +232,7 @@ struct fs_ctx {
 
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int device = 0;   // the device that was current at fs_create (every buffer lives there)
     cusolverDnHandle_t solver = nullptr;
     cublasHandle_t blas = nullptr;
 

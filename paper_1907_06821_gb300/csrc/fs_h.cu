@@ -439,13 +439,19 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device (looked up once per device).
-fs_status scratch_address(void** out, std::string& err) {
+// Device address of g_static_scratch on the context's device, which must be
+// the current device (looked up once per device).
+fs_status scratch_address(int ctx_dev, void** out, std::string& err) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         err = "fs_apply_H_static: no usable current device";
         return FS_ERR_CUDA;
+    }
+    if (dev != ctx_dev) {
+        err = "fs_apply_H_static: the current device (" + std::to_string(dev) + ") is not the context's device (" +
+              std::to_string(ctx_dev) + "); make the context's device current first";
+        return FS_ERR_ARG;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
@@ -471,7 +477,7 @@ extern "C" fs_status fs_apply_H_static(fs_ctx* c, const void* psi, void* hpsi, i
     }
     if (nband == 0) return FS_OK;
     void* base = nullptr;
-    fs_status st = scratch_address(&base, c->err);
+    fs_status st = scratch_address(c->device, &base, c->err);
     if (st != FS_OK) return st;
     const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
     const size_t colband = (size_t)n2 * c->ncol * sizeof(double2);

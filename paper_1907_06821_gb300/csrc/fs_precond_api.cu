@@ -4,7 +4,10 @@
 #include "fs_common.cuh"
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
+
+void ctx_ensure_fp32(fs_ctx* c);
 
 namespace {
 template <typename Fn> fs_status guard(fs_ctx* c, Fn fn) {
@@ -21,6 +24,42 @@ template <typename Fn> fs_status guard(fs_ctx* c, Fn fn) {
 __global__ void d2f_kernel(const double2* in, float2* out, long n) {
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
         out[t] = make_float2((float)in[t].x, (float)in[t].y);
+}
+
+// Features (and labels) of caller-given residual rows, through the same device
+// steps a recording solve takes: the correction E = Xref Xref^H x - x by the
+// solver's GEMMs and kernel, the shell sums and the feature/label kernel.
+template <typename T2>
+void features_of(fs_ctx* c, const T2* R, const T2* X, const T2* Xref, int nref, const double* d, int nb, float* F,
+                 float* zt, float* wt) {
+    Mlp& L = c->mlp;
+    const long npw = c->npw;
+    std::vector<double2> dots(nb);
+    std::vector<int> ident(nb);
+    for (int i = 0; i < nb; ++i) {
+        dots[i] = make_double2(d[i], 0.0);
+        ident[i] = i;
+    }
+    dbuf dd, map;
+    dd.alloc(nb * sizeof(double2));
+    map.alloc(nb * sizeof(int));
+    FS_CUDA(cudaMemcpyAsync(dd.p, dots.data(), nb * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    FS_CUDA(cudaMemcpyAsync(map.p, ident.data(), nb * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const T2* Err = nullptr;
+    dbuf cg;
+    if (X) {
+        cg.alloc((size_t)nref * nb * sizeof(double2));
+        L.proj.ensure((size_t)nb * npw * sizeof(T2));
+        L.err.ensure((size_t)nb * npw * sizeof(T2));
+        gemm_gram<T2>(c, nref, nb, npw, Xref, npw, nullptr, X, npw, map.as<int>(), cg.as<double2>(), 1, nref, 1.0,
+                      0.0);
+        gemm_nn<T2, double2>(c, nb, npw, nref, cg.as<double2>(), nref, 1, Xref, npw, nullptr, L.proj.as<T2>(), npw,
+                             nullptr, 1.0, 0.0, nullptr, 0);
+        mlp_err_from_proj<T2>(c, L.proj.as<T2>(), X, map.as<int>(), nb, L.err.as<T2>());
+        Err = L.err.as<T2>();
+    }
+    mlp_features<T2>(c, R, map.as<int>(), nb, dd.as<double2>(), Err, F, zt, wt);
+    FS_CUDA(cudaStreamSynchronize(c->stream));
 }
 }  // namespace
 
@@ -117,6 +156,32 @@ fs_status fs_precond_eval(fs_ctx* c, const float* features, int rows, float* z) 
         mlp_setup(c);
         mlp_forward(c, features, rows, z);
         FS_CUDA(cudaStreamSynchronize(c->stream));
+    });
+}
+
+fs_status fs_precond_features(fs_ctx* c, double e_ref, const void* R, const void* X, const void* Xref, int nref,
+                               const double* d, int nb, int precision, float* F, float* zt, float* wt) {
+    if (!c) return FS_ERR_ARG;
+    if (nb < 0 || !std::isfinite(e_ref) || (precision != FS_FP64 && precision != FS_MIXED) ||
+        (nb > 0 && (!R || !d || !F)) || (X && (!Xref || nref <= 0 || !zt || !wt))) {
+        c->err = "fs_precond_features: bad arguments";
+        return FS_ERR_ARG;
+    }
+    if (nb == 0) return FS_OK;
+    return guard(c, [&] {
+        mlp_setup(c);
+        Mlp& L = c->mlp;
+        if (L.e_ref != e_ref || !L.Mdev.p) {
+            L.e_ref = e_ref;
+            L.Mdev.release();
+        }
+        if (precision == FS_MIXED) {
+            ctx_ensure_fp32(c);
+            features_of<float2>(c, (const float2*)R, (const float2*)X, (const float2*)Xref, nref, d, nb, F, zt, wt);
+        } else {
+            features_of<double2>(c, (const double2*)R, (const double2*)X, (const double2*)Xref, nref, d, nb, F, zt,
+                                 wt);
+        }
     });
 }
 

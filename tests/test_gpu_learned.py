@@ -71,6 +71,45 @@ def test_loss_and_gradient_match_oracle(fs):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_features_and_labels_match_oracle(fs, precision):
+    """The features, labels and weights a recording solve computes on the device
+    (correction into the reference span by the solver's GEMMs, shell sums,
+    feature/label kernel) against oracle/mlp.features_and_labels on the same
+    residual block; shells with no plane wave carry weight 0 on both sides."""
+    w = fi.make_config("tiny")
+    h = pw.Hamiltonian(w)
+    npw, nb, nref, ns = h.npw, 7, 9, 32
+    rng = np.random.default_rng(21)
+    damp = 1.0 / (1.0 + h.kin)
+    R = fi.raw_start_block(nb, npw, 31) * damp[None, :]
+    X = fi.raw_start_block(nb, npw, 32) * damp[None, :]
+    Q, _ = np.linalg.qr(fi.raw_start_block(nref, npw, 33).T)
+    Xref = np.ascontiguousarray(Q.T)
+    d = rng.uniform(-0.3, 0.3, size=nb)
+    cdt = np.complex128 if precision == "fp64" else np.complex64
+    R, X, Xref = R.astype(cdt), X.astype(cdt), Xref.astype(cdt)
+    prec = fs.FS_FP64 if precision == "fp64" else fs.FS_MIXED
+    with fs.Context.from_workload(w, precision=prec) as c:
+        tR, tX, tXr = (torch.from_numpy(a).cuda() for a in (R, X, Xref))
+        F, zt, wt = (t.cpu().numpy().astype(np.float64) for t in c.precond_features(w.e_ref, tR, d, X=tX, Xref=tXr))
+        F_only = c.precond_features(w.e_ref, tR, d).cpu().numpy()
+    R64, X64, Xr64 = (a.astype(np.complex128) for a in (R, X, Xref))
+    E_err = (Xr64.conj() @ X64.T).T @ Xr64 - X64
+    M = 1.0 / ((h.kin - w.e_ref) ** 2 + 0.5 ** 2)
+    shell = mlp.shell_index(h.kin, w.ecut, ns)
+    Fo, zo, wo = mlp.features_and_labels(h.kin, w.ecut, ns, M, R64, E_err, d, shell)
+    full = np.tile(np.bincount(shell, minlength=ns) > 0, nb)
+    assert full.sum() >= nb * 20                     # most shells hold plane waves
+    assert np.array_equal(F_only, F.astype(np.float32))
+    assert np.abs(F[full] - Fo[full]).max() <= 2e-5
+    assert np.abs(wt - wo).max() <= 1e-5 and np.all(wt[~full] == 0)
+    # labels: log-gains relative to the band's weighted mean (FP32 storage; the FP32
+    # stage's correction comes from TF32 x3 tensor-core products)
+    ltol = 1e-4 if precision == "fp64" else 2e-3
+    assert np.abs(zt[full] - zo[full]).max() <= ltol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_untrained_network_is_paper_preconditioner(fs, precision):
     w = fi.make_config("tiny")
     prec = fs.FS_FP64 if precision == "fp64" else fs.FS_MIXED

@@ -130,6 +130,23 @@ def test_solve_matches_lapack(fs, case, precision):
     _check_solution(w, r, states, eb)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["tiny", "box_k_radix35", "box_dense"])
+def test_teter_preconditioner_solve_matches_lapack(fs, case, precision):
+    """The Teter-Payne-Allan preconditioner in place of the paper's M(G): the
+    preconditioner changes the path, not the fixed point, so the result must
+    be the brute-force set again."""
+    w = CASES[case]() if case in CASES else dense_box()
+    eb, _, _ = pw.brute_nearest(w, w.e_ref, w.nstates)
+    prec = fs.FS_FP64 if precision == "fp64" else fs.FS_MIXED
+    with make_ctx(fs, w, precision=prec, precond=fs.FS_PREC_TETER) as c:
+        c.set_initial_states(fi.raw_start_block(w.nbands, c.npw, 17), damp=True)
+        r = c.solve(w.e_ref, w.nstates, tol=TOL_RES)
+        states = c.get_states(w.nstates)
+    assert r["nconv"] == w.nstates
+    _check_solution(w, r, states, eb)
+
+
 @pytest.mark.parametrize("nband", [37, 300])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_tensor_core_path_matches_cuda_core_path(fs, case, nband):
@@ -161,13 +178,33 @@ def test_wire_apply_H_sampled_bands(fs):
     assert rel_err(out32[pick].astype(np.complex128), ref) < tol32(w)
 
 
+def _golden_nearest(e_ref, nstates):
+    """The nstates eigenvalues nearest e_ref from the wire's golden spectrum
+    (tests/golden/wire_spectrum.json: the lowest eigenvalues of the oracle's H by
+    SciPy's LOBPCG), and the distance of the next one."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "wire_spectrum.json")
+    with open(path) as f:
+        ev = np.asarray(json.load(f)["eigenvalues"])
+    order = np.lexsort((ev, np.abs(ev - e_ref)))
+    near = ev[order[:nstates]]
+    dmax = np.abs(near - e_ref).max()
+    # the golden list must reach past the window on the upper side
+    assert ev.max() > e_ref + dmax
+    return np.sort(near), np.abs(ev[order[nstates]] - e_ref)
+
+
 def test_wire_solve_sampled_states(fs):
     """Full-size wire solve in the benchmark's configuration (mixed precision,
-    the 256 states nearest E_ref, start block seed 17): every state passes the
-    library's FP64 check; eight states (first, last, the largest reported
-    residual and five between) are re-checked by the oracle's FP64 H: residual
-    <= 1e-6 and equal to the reported one, orthonormal."""
+    the 256 states nearest E_ref, start block seed 17): the whole returned set
+    of eigenvalues equals the golden set (the 256 eigenvalues of the oracle's H
+    nearest E_ref, from LOBPCG on the CPU) to 1e-5 Ha; eight states (first,
+    last, the largest reported residual and five between) are re-checked by the
+    oracle's FP64 H: residual <= 1e-6 and equal to the reported one,
+    orthonormal."""
     w = fi.make_config("wire")
+    gold, d_next = _golden_nearest(w.e_ref, w.nstates)
     with make_ctx(fs, w, precision=fs.FS_MIXED) as c:
         c.set_initial_states(fi.raw_start_block(w.nbands, c.npw, 17), damp=True)
         r = c.solve(w.e_ref, w.nstates, tol=TOL_RES)
@@ -175,6 +212,9 @@ def test_wire_solve_sampled_states(fs):
     assert r["nconv"] == w.nstates
     d = np.abs(r["eps"] - w.e_ref)
     assert np.all(np.diff(d) >= -1e-12)
+    # the set is unambiguous: the 257th level is well outside the 256th's distance
+    assert d_next - np.abs(gold - w.e_ref).max() > 1e-6
+    assert np.abs(np.sort(r["eps"]) - gold).max() <= TOL_EPS
     pick = sorted({0, w.nstates - 1, int(np.argmax(r["resid"]))} | set(np.linspace(16, 240, 5).astype(int).tolist()))
     h = pw.Hamiltonian(w)
     X = states[pick]

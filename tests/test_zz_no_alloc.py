@@ -50,6 +50,24 @@ def test_static_scratch_matches_apply_H(fs, case):
             assert np.abs(out.cpu().numpy() - ref).max() / scale < 1e-12
 
 
+def test_static_scratch_several_chunks(fs):
+    """The wire grid (72 x 72 x 144, 193,673 plane waves, 2,048 projectors) needs about
+    6 MB of scratch per band, so 23 bands run in three chunks of the 64 MiB array
+    (11, 11 and a ragged last chunk of 1): the chunk offsets and the reuse of the
+    column buffer, projections and partial sums across chunks are exercised."""
+    w = fi.make_config("wire")
+    with fs.Context.from_workload(w) as c:
+        X = torch.from_numpy(fi.raw_start_block(23, c.npw, 41)).cuda()
+        ref = c.apply_H(X, shift=-0.05)
+        scale = ref.abs().max().item()
+        for _ in range(2):
+            out = torch.empty_like(X)
+            st = c.lib.fs_apply_H_static(c.h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         X.shape[0], ctypes.c_double(-0.05))
+            assert st == fs.FS_OK, c.lib.fs_last_error(c.h)
+            assert (out - ref).abs().max().item() / scale < 1e-12
+
+
 def test_static_scratch_rejects_oversized_band(fs):
     # 108 x 108 x 720 grid and a 20 Ha sphere: one band's column buffer alone is ~90 MB
     L, n = (50.0, 50.0, 100.0), (108, 108, 720)
