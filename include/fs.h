@@ -253,9 +253,12 @@ fs_status fs_batch_solve(fs_batch* batch, const double* e_ref, const int* nstate
                          fs_status* status);
 void fs_batch_destroy(fs_batch* batch);
 
-/* FFT tile autotuner: time H applications of 16 bands with 2, 4, 8, 16 and 32
- * z-columns per thread block for this context's grid and precision, keep the
- * fastest (cached per grid shape for the process); *cpb receives it (may be NULL). */
+/* FFT launch-shape autotuner: times H applications of 32 bands for this
+ * context's grid and precision with 2, 4, 8, 16 and 32 z-columns per thread
+ * block, then (register-FFT grids) 1 to 4 line items per thread of the plane
+ * kernel and band chunks of 16 to 96 MiB of column buffer, keeping the fastest
+ * of each in turn (cached per grid shape for the process); *cpb receives the
+ * column tile (may be NULL).  With opts.verbose each timing goes to stderr. */
 fs_status fs_autotune(fs_ctx* ctx, int* cpb);
 
 /* ---- folded-spectrum linear solve (Sec. II.C, Eq. wl1 and the M' preconditioner) ----

@@ -123,12 +123,19 @@ void upload_potential(fs_ctx* c, const double* vloc) {
     const size_t ng = (size_t)n0 * n1 * n2;
     std::vector<double> vz(ng);
     std::vector<float> vzf(ng);
-    for (int x = 0; x < n0; ++x)
-        for (int y = 0; y < n1; ++y)
-            for (int z = 0; z < n2; ++z) {
-                double v = vloc[((size_t)x * n1 + y) * n2 + z];
+    // plane-major [z][x][y]; on the register-FFT path each axis is stored in
+    // the permuted order its inverse transform leaves ([p_z][p_x][p_y])
+    std::vector<int> ix[3];
+    for (int d = 0; d < 3; ++d) {
+        ix[d].resize(c->n[d]);
+        for (int p = 0; p < c->n[d]; ++p) ix[d][p] = c->fast ? fft_perm_index(c, d, p) : p;
+    }
+    for (int pz = 0; pz < n2; ++pz)
+        for (int px = 0; px < n0; ++px)
+            for (int py = 0; py < n1; ++py) {
+                double v = vloc[((size_t)ix[0][px] * n1 + ix[1][py]) * n2 + ix[2][pz]];
                 if (!std::isfinite(v)) throw fs_error(FS_ERR_ARG, "vloc holds NaN/Inf");
-                size_t o = (size_t)z * n0 * n1 + (size_t)x * n1 + y;
+                size_t o = (size_t)pz * n0 * n1 + (size_t)px * n1 + py;
                 vz[o] = v;
                 vzf[o] = (float)v;
             }

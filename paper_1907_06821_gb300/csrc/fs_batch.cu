@@ -6,6 +6,7 @@
 #include "fs_common.cuh"
 
 #include <algorithm>
+#include <cstdio>
 #include <atomic>
 #include <chrono>
 #include <map>
@@ -22,7 +23,11 @@ struct fs_batch {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, int> g_tuned;  // (n0, n1, n2, ncol, fp32) -> columns per block
+struct Tuned {
+    int cpb, ipt;
+    size_t chunk;
+};
+std::map<std::tuple<int, int, int, int, int>, Tuned> g_tuned;  // (n0, n1, n2, ncol, fp32) -> launch shapes
 
 template <typename T2> double time_apply(fs_ctx* c, int nb, int reps) {
     dbuf in, out;
@@ -47,9 +52,11 @@ template <typename T2> double time_apply(fs_ctx* c, int nb, int reps) {
 
 extern "C" {
 
-// Pick the column-kernel tile (z-columns per thread block) for this context's
-// grid by timing H applications with each candidate; results are cached per
-// grid shape for the process.
+// Pick the FFT launch shapes for this context's grid by timing H applications
+// of 32 bands with each candidate (coordinate descent: column tile of the z
+// kernels, then line items per thread of the plane kernel, then the band
+// chunk whose column buffer stays in L2); results are cached per grid shape
+// and precision for the process.  verbose > 0 prints each timing on stderr.
 fs_status fs_autotune(fs_ctx* c, int* cpb_out) {
     if (!c) return FS_ERR_ARG;
     try {
@@ -59,30 +66,63 @@ fs_status fs_autotune(fs_ctx* c, int* cpb_out) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tuned.find(key);
             if (it != g_tuned.end()) {
-                c->cpb = it->second;
+                c->cpb = it->second.cpb;
+                c->pf_ipt = it->second.ipt;
+                c->hchunk_bytes = it->second.chunk;
                 if (cpb_out) *cpb_out = c->cpb;
                 return FS_OK;
             }
         }
-        const size_t esz = fp32 ? sizeof(float2) : sizeof(double2);
-        const int nb = 16;
+        const int nb = 32;
+        auto time_now = [&]() { return fp32 ? time_apply<float2>(c, nb, 3) : time_apply<double2>(c, nb, 3); };
+        auto report = [&](const char* what, int v, double ms) {
+            if (c->opt.verbose) fprintf(stderr, "[fs] autotune %s %d: %.3f ms for %d bands\n", what, v, ms, nb);
+        };
+        // column tile; it serves both precisions of a mixed solve, so it is sized for FP64
         int best = c->cpb;
         double best_ms = 1e300;
         for (int cand : {2, 4, 8, 16, 32}) {
-            if ((size_t)cand * c->n[2] * esz > 200 * 1024) continue;
+            const size_t need = c->fast ? ((size_t)cand * c->Pz + c->n[2]) * sizeof(double2)
+                                        : (size_t)cand * c->n[2] * sizeof(double2);
+            if (need > 200 * 1024) continue;
             c->cpb = cand;
-            double ms = fp32 ? time_apply<float2>(c, nb, 3) : time_apply<double2>(c, nb, 3);
+            const double ms = time_now();
+            report("z-column tile", cand, ms);
             if (ms < best_ms) {
                 best_ms = ms;
                 best = cand;
             }
         }
         c->cpb = best;
+        if (c->fast) {
+            int bi = c->pf_ipt;
+            for (int ipt : {1, 2, 3, 4}) {
+                c->pf_ipt = ipt;
+                const double ms = time_now();
+                report("plane items per thread", ipt, ms);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bi = ipt;
+                }
+            }
+            c->pf_ipt = bi;
+            size_t bc = c->hchunk_bytes;
+            for (size_t mb : {16, 32, 48, 64, 96}) {
+                c->hchunk_bytes = mb << 20;
+                const double ms = time_now();
+                report("chunk MiB", (int)mb, ms);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bc = mb << 20;
+                }
+            }
+            c->hchunk_bytes = bc;
+        }
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned[key] = best;
+            g_tuned[key] = Tuned{c->cpb, c->pf_ipt, c->hchunk_bytes};
         }
-        if (cpb_out) *cpb_out = best;
+        if (cpb_out) *cpb_out = c->cpb;
         c->err.clear();
         return FS_OK;
     } catch (const fs_error& e) {

@@ -58,6 +58,14 @@ template <typename T2> struct FftPlan {
     const T2* tw;
 };
 
+// Geometry of one line family of the register FFTs (fs_fft.cuh): length
+// L = A * B, element stride es (in elements), block pitch Bp = B + pad (pad 0
+// or 1 slot after every block of B positions).
+struct LineGeo {
+    int L, A, B, Bp, es;
+};
+__host__ __device__ inline int geo_slot(const LineGeo& g, int p) { return p + (g.Bp - g.B) * (p / g.B); }
+
 // ------------------------------------------------------------------ errors
 #define FS_CUDA(call)                                                                    \
     do {                                                                                 \
@@ -249,6 +257,19 @@ struct fs_ctx {
     FftPlan<double2> plan64[3];
     FftPlan<float2> plan32[3];
     int cpb = 16;     // columns per block in the column kernels
+    // register-FFT path: line geometries of x (rows of a plane), y (within a
+    // row, padded) and z (columns, padded); row pitch P of a plane, line pitch
+    // Pz of a column tile; rows of a plane that hold sphere columns; per-column
+    // slot in the plane (x P + y slot); per sphere entry its column and z slot
+    // packed as (column << 16 | z slot).  V(r) (vz64/vz32) is then stored in
+    // the permuted layout [p_z][p_x][p_y].
+    bool fast = false;
+    bool zbig = false;  // the z split needs the large register DFT sizes (16, 27)
+    LineGeo gx{}, gy{}, gz{};
+    int P = 0, Pz = 0, nxr = 0, pf_items = 0;  // pf_items: line items of the busiest plane pass
+    int pf_ipt = 4;                              // items per thread of the plane kernel
+    dbuf xrows, col_slot, ent_cz;
+    size_t hchunk_bytes = 96ull << 20;  // column-buffer bytes per band chunk (kept in L2 between passes)
 
     // projectors
     dbuf beta64;      // double2 [nptot][npw]
@@ -308,6 +329,7 @@ template <typename T2>
 void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, const int* rowmap_in = nullptr);
 
 void ctx_prepare_fft(fs_ctx* c);
+int fft_perm_index(const fs_ctx* c, int d, int p);  // spatial index at position p of axis d (register-FFT path)
 
 // folded linear solve (fs_linear.cu): device w and psi [nrhs][npw] complex128
 fs_status linear_solve_impl(fs_ctx* c, double e_ref, const double2* w, double2* psi, int nrhs, bool from_psi,

@@ -12,68 +12,10 @@
 //                    entries and add (|q|^2/2 - shift) psi.
 // Nonlocal part: P = B^H psi (Gram GEMM), Q = D P per atom, hpsi += B Q.
 #include "fs_common.cuh"
+#include "fs_fft.cuh"
 
 #include <algorithm>
 #include <cmath>
-
-// ------------------------------------------------------------------ radix butterflies
-// out[k] = sum_r v[r] exp(s * 2 pi i r k / R), s = +1 (inverse) or -1 (forward)
-template <typename T2> __device__ __forceinline__ T2 mul_si(T2 a, int s) {  // a * (s i)
-    return s > 0 ? mk(-a.y, a.x) : mk(a.y, -a.x);
-}
-
-template <typename T2, int R> struct Bfly;
-
-template <typename T2> struct Bfly<T2, 2> {
-    __device__ __forceinline__ static void run(T2* v, int) {
-        T2 a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
-    }
-};
-
-template <typename T2> struct Bfly<T2, 4> {
-    __device__ __forceinline__ static void run(T2* v, int s) {
-        T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        T2 t2 = cadd(v[1], v[3]), t3 = mul_si(csub(v[1], v[3]), s);
-        v[0] = cadd(t0, t2);
-        v[2] = csub(t0, t2);
-        v[1] = cadd(t1, t3);
-        v[3] = csub(t1, t3);
-    }
-};
-
-template <typename T2> struct Bfly<T2, 3> {
-    __device__ __forceinline__ static void run(T2* v, int s) {
-        using R = typename real_of<T2>::t;
-        const R h = (R)0.86602540378443864676;  // sqrt(3)/2
-        T2 t = cadd(v[1], v[2]);
-        T2 d = mul_si(cscale(csub(v[1], v[2]), h), s);
-        T2 a = csub(v[0], cscale(t, (R)0.5));
-        v[0] = cadd(v[0], t);
-        v[1] = cadd(a, d);
-        v[2] = csub(a, d);
-    }
-};
-
-template <typename T2> struct Bfly<T2, 5> {
-    __device__ __forceinline__ static void run(T2* v, int s) {
-        using R = typename real_of<T2>::t;
-        const R c1 = (R)0.30901699437494742410, c2 = (R)-0.80901699437494742410;
-        const R s1 = (R)0.95105651629515357212, s2 = (R)0.58778525229247312917;
-        T2 a14 = cadd(v[1], v[4]), d14 = csub(v[1], v[4]);
-        T2 a23 = cadd(v[2], v[3]), d23 = csub(v[2], v[3]);
-        T2 r1 = cadd(v[0], cadd(cscale(a14, c1), cscale(a23, c2)));
-        T2 r2 = cadd(v[0], cadd(cscale(a14, c2), cscale(a23, c1)));
-        T2 i1 = mul_si(cadd(cscale(d14, s1), cscale(d23, s2)), s);
-        T2 i2 = mul_si(csub(cscale(d14, s2), cscale(d23, s1)), s);
-        v[0] = cadd(v[0], cadd(a14, a23));
-        v[1] = cadd(r1, i1);
-        v[4] = csub(r1, i1);
-        v[2] = cadd(r2, i2);
-        v[3] = csub(r2, i2);
-    }
-};
 
 // q = a / d (integer quotient) for 0 <= a < 2^22, d >= 1, without an integer
 // division: (a + 1/2) / d = q + (r + 1/2) / d lies at least 1/(2d) from the
@@ -260,6 +202,229 @@ __global__ void apply_D_kernel(const T2* __restrict__ P, T2* __restrict__ Q, con
     }
 }
 
+// ------------------------------------------------------------------ register-FFT kernels
+// The same three passes with every line transformed by the two-pass register
+// scheme of fs_fft.cuh.  The z axis of the column buffer, and the x and y axes
+// inside a plane, are carried in the permuted layout the inverse transforms
+// leave; V(r) is stored permuted the same way (context set-up), so the
+// multiply needs no reordering.
+constexpr int ZF_THREADS = 256;
+constexpr int PF_MAX_THREADS = 768;
+
+// unpack the sphere z-columns of a tile, inverse z-FFT, write [band][p_z][column]
+template <typename T2, bool BIG>
+__global__ void __launch_bounds__(ZF_THREADS)
+zinv_kernel(const T2* __restrict__ psi, const int* __restrict__ rowmap, long ldpsi, T2* __restrict__ colbuf,
+            const int* __restrict__ col_start, const int* __restrict__ ent_cz, int ncol, int cpb, LineGeo gz, int Pz,
+            const T2* __restrict__ twz) {
+    using R = typename real_of<T2>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* tw = reinterpret_cast<T2*>(smem_raw);
+    T2* lines = tw + gz.L;
+    const int band = blockIdx.y, c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+    const long src = rowmap ? rowmap[band] : band;
+    for (int i = threadIdx.x; i < gz.L; i += blockDim.x) tw[i] = twz[i];
+    for (int i = threadIdx.x; i < nc * Pz; i += blockDim.x) lines[i] = mk((R)0, (R)0);
+    __syncthreads();
+    const int g0 = col_start[c0], g1 = col_start[c0 + nc];
+    const T2* p = psi + src * ldpsi;
+    // four loads in flight per thread before the shared-memory stores
+    for (int g = g0 + threadIdx.x; g < g1; g += 4 * blockDim.x) {
+        T2 v[4];
+        int e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int gg = g + u * blockDim.x;
+            if (gg < g1) {
+                v[u] = p[gg];
+                e[u] = ent_cz[gg];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (g + u * (int)blockDim.x < g1) lines[((e[u] >> 16) - c0) * Pz + (e[u] & 0xFFFF)] = v[u];
+    }
+    __syncthreads();
+    // lanes of a warp: the same role in consecutive lines
+    for (int i = threadIdx.x; i < nc * gz.B; i += blockDim.x) {
+        const int r = i / nc;
+        stride_pass<+1, true, BIG>(lines + (i - r * nc) * Pz, gz, r, tw);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * gz.A; i += blockDim.x) {
+        const int k = i / nc;
+        block_pass<+1, false, BIG>(lines + (i - k * nc) * Pz, gz, k, tw);
+    }
+    __syncthreads();
+    T2* out = colbuf + (long)band * gz.L * ncol + c0;
+    for (int i = threadIdx.x; i < nc * gz.L; i += blockDim.x) {
+        const int pz = i / nc, cc = i - pz * nc;
+        out[(long)pz * ncol + cc] = lines[cc * Pz + line_slot(gz, pz)];
+    }
+}
+
+// inverse x pass 2, x V(r), forward x pass 1 on the block k1 of one x line
+template <int B, typename T2, typename R>
+__device__ __forceinline__ void fused_v_block(T2* line, const LineGeo& g, int k1, const T2* tw,
+                                              const R* __restrict__ v, int vstride) {
+    T2 a[B];
+    const int base = g.Bp * k1;
+#pragma unroll
+    for (int j = 0; j < B; ++j) a[j] = line[(base + j) * g.es];
+    RDft<B>::template run<+1>(a, tw, g.A);
+#pragma unroll
+    for (int j = 0; j < B; ++j) a[j] = cscale(a[j], __ldg(v + (long)(g.B * k1 + j) * vstride));
+    RDft<B>::template run<-1>(a, tw, g.A);
+#pragma unroll
+    for (int m = 1; m < B; ++m)
+        if (k1) a[m] = cmul(a[m], twid<-1>(tw, k1 * m));
+#pragma unroll
+    for (int j = 0; j < B; ++j) line[(base + j) * g.es] = a[j];
+}
+
+template <typename T2, typename R>
+__device__ __forceinline__ void fused_v(T2* line, const LineGeo& g, int k1, const T2* tw, const R* v, int vstride) {
+    switch (g.B) {
+#define FS_CASE(n) \
+    case n: fused_v_block<n>(line, g, k1, tw, v, vstride); break;
+        FS_FFT_SIZES_S(FS_CASE)
+#undef FS_CASE
+        default: break;
+    }
+}
+
+// One (band, z position) plane: scatter the columns, inverse y on the rows that
+// hold columns, inverse x, x V(r), forward x, forward y on those rows, gather.
+template <typename T2, typename R>
+__global__ void __launch_bounds__(sizeof(T2) == 16 ? PF_MAX_THREADS / 2 : PF_MAX_THREADS)
+plane_fast_kernel(T2* __restrict__ colbuf, const int* __restrict__ col_slot, int ncol,
+                  const int* __restrict__ xrows, int nxr, const R* __restrict__ vperm, LineGeo gx, LineGeo gy, int P,
+                  const T2* __restrict__ twx_g, const T2* __restrict__ twy_g) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n0 = gx.L, n1 = gy.L, nz = gridDim.x;
+    T2* twx = reinterpret_cast<T2*>(smem_raw);
+    T2* twy = twx + n0;
+    T2* plane = twy + n1;
+    const int pz = blockIdx.x, band = blockIdx.y;
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) twx[i] = twx_g[i];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) twy[i] = twy_g[i];
+    for (int i = threadIdx.x; i < n0 * P; i += blockDim.x) plane[i] = mk((R)0, (R)0);
+    __syncthreads();
+    T2* cb = colbuf + ((long)band * nz + pz) * ncol;
+    for (int c = threadIdx.x; c < ncol; c += 4 * blockDim.x) {
+        T2 v[4];
+        int e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int cc = c + u * blockDim.x;
+            if (cc < ncol) {
+                v[u] = cb[cc];
+                e[u] = col_slot[cc];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (c + u * (int)blockDim.x < ncol) plane[e[u]] = v[u];
+    }
+    __syncthreads();
+    // y passes: lanes of a warp take the same role in consecutive rows
+    for (int i = threadIdx.x; i < nxr * gy.B; i += blockDim.x) {
+        const int r = i / nxr;
+        stride_pass<+1, true, false>(plane + xrows[i - r * nxr] * P, gy, r, twy);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nxr * gy.A; i += blockDim.x) {
+        const int k = i / nxr;
+        block_pass<+1, false, false>(plane + xrows[i - k * nxr] * P, gy, k, twy);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1 * gx.B; i += blockDim.x) {
+        const int r = i / n1, q = i - r * n1;
+        stride_pass<+1, true, false>(plane + line_slot(gy, q), gx, r, twx);
+    }
+    __syncthreads();
+    const R* vz = vperm + (long)pz * n0 * n1;
+    for (int i = threadIdx.x; i < n1 * gx.A; i += blockDim.x) {
+        const int k = i / n1, q = i - k * n1;
+        fused_v(plane + line_slot(gy, q), gx, k, twx, vz + q, n1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n1 * gx.B; i += blockDim.x) {
+        const int r = i / n1, q = i - r * n1;
+        stride_pass<-1, false, false>(plane + line_slot(gy, q), gx, r, twx);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nxr * gy.A; i += blockDim.x) {
+        const int k = i / nxr;
+        block_pass<-1, true, false>(plane + xrows[i - k * nxr] * P, gy, k, twy);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nxr * gy.B; i += blockDim.x) {
+        const int r = i / nxr;
+        stride_pass<-1, false, false>(plane + xrows[i - r * nxr] * P, gy, r, twy);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) cb[c] = plane[col_slot[c]];
+}
+
+// forward z-FFT of a tile of columns, x 1/N, pick the sphere entries, + (|q|^2/2 - shift) psi
+template <typename T2, bool BIG>
+__global__ void __launch_bounds__(ZF_THREADS)
+zfwd_kernel(const T2* __restrict__ colbuf, const T2* __restrict__ psi, const int* __restrict__ rowmap, long ldpsi,
+            T2* __restrict__ hpsi, const int* __restrict__ col_start, const int* __restrict__ ent_cz,
+            const double* __restrict__ kin, int ncol, int cpb, LineGeo gz, int Pz, const T2* __restrict__ twz,
+            double inv_ng, double shift, long npw) {
+    using R = typename real_of<T2>::t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* tw = reinterpret_cast<T2*>(smem_raw);
+    T2* lines = tw + gz.L;
+    const int band = blockIdx.y, c0 = blockIdx.x * cpb, nc = min(cpb, ncol - c0);
+    for (int i = threadIdx.x; i < gz.L; i += blockDim.x) tw[i] = twz[i];
+    const T2* in = colbuf + (long)band * gz.L * ncol + c0;
+    const int tot = nc * gz.L;
+    for (int i = threadIdx.x; i < tot; i += 4 * blockDim.x) {
+        T2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ii = i + u * blockDim.x;
+            if (ii < tot) {
+                const int pz = ii / nc, cc = ii - pz * nc;
+                v[u] = in[(long)pz * ncol + cc];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int ii = i + u * blockDim.x;
+            if (ii < tot) {
+                const int pz = ii / nc, cc = ii - pz * nc;
+                lines[cc * Pz + line_slot(gz, pz)] = v[u];
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * gz.A; i += blockDim.x) {
+        const int k = i / nc;
+        block_pass<-1, true, BIG>(lines + (i - k * nc) * Pz, gz, k, tw);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nc * gz.B; i += blockDim.x) {
+        const int r = i / nc;
+        stride_pass<-1, false, BIG>(lines + (i - r * nc) * Pz, gz, r, tw);
+    }
+    __syncthreads();
+    const int g0 = col_start[c0], g1 = col_start[c0 + nc];
+    const long src = rowmap ? rowmap[band] : band;
+    const T2* p = psi + src * ldpsi;
+    T2* o = hpsi + (long)band * npw;
+    for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+        const int e = ent_cz[g];
+        T2 a = lines[((e >> 16) - c0) * Pz + (e & 0xFFFF)];
+        T2 x = p[g];
+        R f = (R)(kin[g] - shift);
+        o[g] = mk((R)(a.x * (R)inv_ng) + f * x.x, (R)(a.y * (R)inv_ng) + f * x.y);
+    }
+}
+
 // ------------------------------------------------------------------ host side
 static int col_smem(int cpb, int n2, size_t esz) { return (int)(cpb * n2 * esz); }
 
@@ -293,6 +458,84 @@ static int group_lines(int n, const std::vector<int>& rads, int threads, int ept
 template <typename T2> static void set_attr_smem(const void* fn, int bytes) {
     (void)bytes;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+// A = B * ... : the split L = A * B (A >= B, both register DFT sizes) with the smallest A.
+static bool pick_split(int L, int& A, int& B) {
+    A = 0;
+    for (int b = 1; b * b <= L; ++b) {
+        if (L % b) continue;
+        const int a = L / b;
+        if (fft_size_ok(a) && fft_size_ok(b) && (A == 0 || a < A)) {
+            A = a;
+            B = b;
+        }
+    }
+    return A > 0;
+}
+
+static inline int posmod_(int a, int n) { return ((a % n) + n) % n; }
+
+// Plan of the register-FFT path (fs_fft.cuh) when every axis splits into
+// register DFT sizes and the padded plane fits in shared memory in FP64.
+static void prepare_fast_fft(fs_ctx* c) {
+    c->fast = false;
+    LineGeo g[3];
+    for (int d = 0; d < 3; ++d) {
+        int A = 0, B = 0;
+        if (!pick_split(c->n[d], A, B)) return;
+        if (d < 2 && !(fft_size_small(A) && fft_size_small(B))) return;  // plane axes: small register DFTs
+        g[d] = LineGeo{c->n[d], A, B, B, 1};
+    }
+    const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
+    // odd pitches: the lanes of a warp take the same position in consecutive
+    // lines (rows of a plane, columns of a tile), so an odd line pitch spreads
+    // them over all banks
+    const int P = n1 | 1, Pz = n2 | 1;
+    const size_t plane_bytes = ((size_t)n0 * P + n0 + n1) * sizeof(double2);
+    if (plane_bytes > 227 * 1024) return;
+    int cpb = 32;
+    while (cpb > 1 && ((size_t)cpb * Pz + n2) * sizeof(double2) > 100 * 1024) cpb /= 2;
+    g[0].es = P;
+    // columns in sphere order (a new column starts where (g0, g1) changes)
+    if (c->ncol >= (1 << 16) || Pz >= (1 << 16)) return;  // packed (column, z slot) entries
+    std::vector<int> cslot, ecz(c->npw), rows;
+    std::vector<char> has_row(n0, 0);
+    const std::vector<int>& mil = c->miller;
+    for (int i = 0; i < c->npw; ++i) {
+        const int g0 = mil[3 * i], g1 = mil[3 * i + 1], g2 = mil[3 * i + 2];
+        if (i == 0 || g0 != mil[3 * (i - 1)] || g1 != mil[3 * (i - 1) + 1]) {
+            const int x = posmod_(g0, n0);
+            cslot.push_back(x * P + geo_slot(g[1], posmod_(g1, n1)));
+            has_row[x] = 1;
+        }
+        ecz[i] = (((int)cslot.size() - 1) << 16) | geo_slot(g[2], posmod_(g2, n2));
+    }
+    for (int x = 0; x < n0; ++x)
+        if (has_row[x]) rows.push_back(x);
+    if ((int)cslot.size() != c->ncol) return;
+    c->col_slot.alloc(cslot.size() * sizeof(int));
+    c->ent_cz.alloc(ecz.size() * sizeof(int));
+    c->xrows.alloc(rows.size() * sizeof(int));
+    FS_CUDA(cudaMemcpy(c->col_slot.p, cslot.data(), cslot.size() * sizeof(int), cudaMemcpyHostToDevice));
+    FS_CUDA(cudaMemcpy(c->ent_cz.p, ecz.data(), ecz.size() * sizeof(int), cudaMemcpyHostToDevice));
+    FS_CUDA(cudaMemcpy(c->xrows.p, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->gx = g[0];
+    c->gy = g[1];
+    c->gz = g[2];
+    c->P = P;
+    c->Pz = Pz;
+    c->nxr = (int)rows.size();
+    c->pf_items = std::max(n1 * std::max(g[0].A, g[0].B), c->nxr * std::max(g[1].A, g[1].B));
+    c->cpb = cpb;
+    c->zbig = !(fft_size_small(g[2].A) && fft_size_small(g[2].B));
+    c->fast = true;
+}
+
+// spatial index held at position p of an axis in the permuted layout
+int fft_perm_index(const fs_ctx* c, int d, int p) {
+    const LineGeo& g = d == 0 ? c->gx : d == 1 ? c->gy : c->gz;
+    return p / g.B + g.A * (p % g.B);
 }
 
 void ctx_prepare_fft(fs_ctx* c) {
@@ -339,6 +582,17 @@ void ctx_prepare_fft(fs_ctx* c) {
     set_attr_smem<float2>((const void*)col_forward_kernel<float2>, col_smem(c->cpb, c->n[2], sizeof(float2)));
     set_attr_smem<double2>((const void*)plane_kernel<double2, double>, (int)plane64);
     set_attr_smem<float2>((const void*)plane_kernel<float2, float>, (int)(plane64 / 2));
+    set_attr_smem<double2>((const void*)zinv_kernel<double2, true>, 0);
+    set_attr_smem<double2>((const void*)zfwd_kernel<double2, true>, 0);
+    set_attr_smem<float2>((const void*)zinv_kernel<float2, true>, 0);
+    set_attr_smem<float2>((const void*)zfwd_kernel<float2, true>, 0);
+    set_attr_smem<double2>((const void*)zinv_kernel<double2, false>, 0);
+    set_attr_smem<double2>((const void*)zfwd_kernel<double2, false>, 0);
+    set_attr_smem<float2>((const void*)zinv_kernel<float2, false>, 0);
+    set_attr_smem<float2>((const void*)zfwd_kernel<float2, false>, 0);
+    set_attr_smem<double2>((const void*)plane_fast_kernel<double2, double>, 0);
+    set_attr_smem<float2>((const void*)plane_fast_kernel<float2, float>, 0);
+    prepare_fast_fft(c);
 }
 
 template <typename T2> static const void* vz_of(fs_ctx* c);
@@ -348,50 +602,88 @@ template <typename T2> static const T2* beta_of(fs_ctx* c);
 template <> const double2* beta_of<double2>(fs_ctx* c) { return c->beta64.as<double2>(); }
 template <> const float2* beta_of<float2>(fs_ctx* c) { return c->beta32.as<float2>(); }
 
-// Bands are processed in chunks so that the column buffer stays bounded.
+// Local part (kinetic + V) of nbc bands through the column buffer cb:
+// hpsi[b] = FFT(V FFT^-1 psi[b]) / N + (|q|^2/2 - shift) psi[b].  src rows are
+// src[rm[b]] when rm is given, else consecutive.  prof: time each kernel class.
 template <typename T2>
-void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, const int* rowmap) {
+static void local_part(fs_ctx* c, const T2* src, const int* rm, T2* cb, T2* dst, int nbc, double shift, bool prof) {
     using R = typename real_of<T2>::t;
-    if (nb <= 0) return;
     const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
     const long colband = (long)n2 * c->ncol;
-    const long max_chunk_bytes = 2L << 30;  // 2 GiB of column buffer
-    int chunk = (int)std::max(1L, std::min((long)nb, max_chunk_bytes / (colband * (long)sizeof(T2))));
-    c->colbuf.ensure((size_t)chunk * colband * sizeof(T2));
-    T2* cb = c->colbuf.as<T2>();
+    const int cpb = c->cpb;
+    const int ncb = (c->ncol + cpb - 1) / cpb;
+    const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
+    const double colb = (double)nbc * colband * sizeof(T2), sphb = (double)nbc * c->npw * sizeof(T2);
+    const double ng = (double)n0 * n1 * n2;
+    fs_ctx* pc = prof ? c : nullptr;
+    dim3 gc(ncb, nbc), gp(n2, nbc);
+    if (c->fast) {
+        const int zsm = (int)(((size_t)cpb * c->Pz + n2) * sizeof(T2));
+        const int psm = (int)(((size_t)n0 * c->P + n0 + n1) * sizeof(T2));
+        {
+            ProfScope ps(pc, ks_prec<T2>(KS_COL_INV), sphb + colb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
+            auto k = c->zbig ? zinv_kernel<T2, true> : zinv_kernel<T2, false>;
+            k<<<gc, ZF_THREADS, zsm, c->stream>>>(src, rm, c->npw, cb, c->col_start.as<int>(), c->ent_cz.as<int>(),
+                                                  c->ncol, cpb, c->gz, c->Pz, plan_of<T2>(c, 2).tw);
+        }
+        {
+            ProfScope ps(pc, ks_prec<T2>(KS_PLANE), 2.0 * colb + ng * sizeof(R),
+                         2.0 * 5.0 * nbc * ng * std::log2((double)n0 * n1));
+            const int ipt = std::max(1, c->pf_ipt);
+            const int pt = std::min(sizeof(T2) == 16 ? PF_MAX_THREADS / 2 : PF_MAX_THREADS,
+                                    ((c->pf_items + ipt - 1) / ipt + 31) / 32 * 32);
+            plane_fast_kernel<T2, R><<<gp, pt, psm, c->stream>>>(
+                cb, c->col_slot.as<int>(), c->ncol, c->xrows.as<int>(), c->nxr,
+                (const R*)vz_of<T2>(c), c->gx, c->gy, c->P, plan_of<T2>(c, 0).tw, plan_of<T2>(c, 1).tw);
+        }
+        {
+            ProfScope ps(pc, ks_prec<T2>(KS_COL_FWD), colb + 2.0 * sphb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
+            auto k = c->zbig ? zfwd_kernel<T2, true> : zfwd_kernel<T2, false>;
+            k<<<gc, ZF_THREADS, zsm, c->stream>>>(cb, src, rm, c->npw, dst, c->col_start.as<int>(),
+                                                  c->ent_cz.as<int>(), c->kin.as<double>(), c->ncol, cpb, c->gz,
+                                                  c->Pz, plan_of<T2>(c, 2).tw, inv_ng, shift, c->npw);
+        }
+        return;
+    }
     const FftPlan<T2>& px = plan_of<T2>(c, 0);
     const FftPlan<T2>& py = plan_of<T2>(c, 1);
     const FftPlan<T2>& pz = plan_of<T2>(c, 2);
-    const int cpb = c->cpb;
-    const int ncb = (c->ncol + cpb - 1) / cpb;
     const int csm = col_smem(cpb, n2, sizeof(T2));
     const int psm = n0 * n1 * (int)sizeof(T2);
-    const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
+    {
+        ProfScope ps(pc, ks_prec<T2>(KS_COL_INV), sphb + colb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
+        col_inverse_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(src, rm, c->npw, cb, c->col_start.as<int>(),
+                                                                     c->ent_col.as<int>(), c->ent_z.as<int>(),
+                                                                     c->ncol, cpb, pz);
+    }
+    {
+        ProfScope ps(pc, ks_prec<T2>(KS_PLANE), 2.0 * colb + ng * sizeof(R), 2.0 * 5.0 * nbc * ng * std::log2((double)n0 * n1));
+        plane_kernel<T2, R><<<gp, PLANE_THREADS, psm, c->stream>>>(cb, c->col_xy.as<int>(), c->ncol,
+                                                                   (const R*)vz_of<T2>(c), px, py);
+    }
+    {
+        ProfScope ps(pc, ks_prec<T2>(KS_COL_FWD), colb + 2.0 * sphb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
+        col_forward_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(
+            cb, src, rm, c->npw, dst, c->col_start.as<int>(), c->ent_col.as<int>(), c->ent_z.as<int>(),
+            c->kin.as<double>(), c->ncol, cpb, pz, inv_ng, shift, c->npw);
+    }
+}
+
+// Bands are processed in chunks: on the register-FFT path a chunk's column
+// buffer is sized to stay in L2 between the three passes.
+template <typename T2>
+void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, const int* rowmap) {
+    if (nb <= 0) return;
+    const long colband = (long)c->n[2] * c->ncol;
+    const long max_chunk_bytes = c->fast ? (long)c->hchunk_bytes : (2L << 30);
+    int chunk = (int)std::max(1L, std::min((long)nb, max_chunk_bytes / (colband * (long)sizeof(T2))));
+    c->colbuf.ensure((size_t)chunk * colband * sizeof(T2));
+    T2* cb = c->colbuf.as<T2>();
     for (int b0 = 0; b0 < nb; b0 += chunk) {
         int nbc = std::min(chunk, nb - b0);
         const T2* src = rowmap ? psi : psi + (long)b0 * c->npw;
         const int* rm = rowmap ? rowmap + b0 : nullptr;
-        const double colb = (double)nbc * colband * sizeof(T2), sphb = (double)nbc * c->npw * sizeof(T2);
-        const double ng = (double)n0 * n1 * n2;
-        dim3 gc(ncb, nbc);
-        {
-        ProfScope ps(c, ks_prec<T2>(KS_COL_INV), sphb + colb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
-        col_inverse_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(src, rm, c->npw, cb, c->col_start.as<int>(),
-                                                                     c->ent_col.as<int>(), c->ent_z.as<int>(),
-                                                                     c->ncol, cpb, pz);
-        }
-        dim3 gp(n2, nbc);
-        {
-        ProfScope ps(c, ks_prec<T2>(KS_PLANE), 2.0 * colb + ng * sizeof(R), 2.0 * 5.0 * nbc * ng * std::log2((double)n0 * n1));
-        plane_kernel<T2, R><<<gp, PLANE_THREADS, psm, c->stream>>>(cb, c->col_xy.as<int>(), c->ncol,
-                                                                   (const R*)vz_of<T2>(c), px, py);
-        }
-        {
-        ProfScope ps(c, ks_prec<T2>(KS_COL_FWD), colb + 2.0 * sphb, 5.0 * nbc * c->ncol * n2 * std::log2((double)n2));
-        col_forward_kernel<T2><<<gc, COL_THREADS, csm, c->stream>>>(
-            cb, src, rm, c->npw, hpsi + (long)b0 * c->npw, c->col_start.as<int>(), c->ent_col.as<int>(),
-            c->ent_z.as<int>(), c->kin.as<double>(), c->ncol, cpb, pz, inv_ng, shift, c->npw);
-        }
+        local_part<T2>(c, src, rm, cb, hpsi + (long)b0 * c->npw, nbc, shift, true);
         FS_CUDA(cudaGetLastError());
     }
     if (c->nptot > 0) {
@@ -479,8 +771,7 @@ extern "C" fs_status fs_apply_H_static(fs_ctx* c, const void* psi, void* hpsi, i
     void* base = nullptr;
     fs_status st = scratch_address(c->device, &base, c->err);
     if (st != FS_OK) return st;
-    const int n0 = c->n[0], n1 = c->n[1], n2 = c->n[2];
-    const size_t colband = (size_t)n2 * c->ncol * sizeof(double2);
+    const size_t colband = (size_t)c->n[2] * c->ncol * sizeof(double2);
     const size_t projband = (size_t)c->nptot * sizeof(double2);
     // one band needs its column buffer, P and Q, and one split of the Gram partial sums
     const size_t per_band = colband + 3 * projband;
@@ -496,30 +787,13 @@ extern "C" fs_status fs_apply_H_static(fs_ctx* c, const void* psi, void* hpsi, i
     double2* Q = P + (size_t)chunk * c->nptot;
     double2* part = Q + (size_t)chunk * c->nptot;
     const size_t part_bytes = (size_t)FS_STATIC_SCRATCH_BYTES - (size_t)((unsigned char*)part - s);
-    const FftPlan<double2>& px = c->plan64[0];
-    const FftPlan<double2>& py = c->plan64[1];
-    const FftPlan<double2>& pz = c->plan64[2];
-    const int cpb = c->cpb;
-    const int ncb = (c->ncol + cpb - 1) / cpb;
-    const int csm = col_smem(cpb, n2, sizeof(double2));
-    const int psm = n0 * n1 * (int)sizeof(double2);
-    const double inv_ng = 1.0 / ((double)n0 * n1 * n2);
     const double2* in = static_cast<const double2*>(psi);
     double2* out = static_cast<double2*>(hpsi);
     for (int b0 = 0; b0 < nband; b0 += chunk) {
         const int nbc = std::min(chunk, nband - b0);
         const double2* src = in + (long)b0 * c->npw;
         double2* dst = out + (long)b0 * c->npw;
-        dim3 gc(ncb, nbc);
-        col_inverse_kernel<double2><<<gc, COL_THREADS, csm, c->stream>>>(src, nullptr, c->npw, cb,
-                                                                         c->col_start.as<int>(), c->ent_col.as<int>(),
-                                                                         c->ent_z.as<int>(), c->ncol, cpb, pz);
-        dim3 gp(n2, nbc);
-        plane_kernel<double2, double><<<gp, PLANE_THREADS, psm, c->stream>>>(cb, c->col_xy.as<int>(), c->ncol,
-                                                                             c->vz64.as<double>(), px, py);
-        col_forward_kernel<double2><<<gc, COL_THREADS, csm, c->stream>>>(
-            cb, src, nullptr, c->npw, dst, c->col_start.as<int>(), c->ent_col.as<int>(), c->ent_z.as<int>(),
-            c->kin.as<double>(), c->ncol, cpb, pz, inv_ng, shift, c->npw);
+        local_part<double2>(c, src, nullptr, cb, dst, nbc, shift, false);
         if (c->nptot > 0) {
             if (!gemm_gram_scratch<double2>(c->stream, c->nptot, nbc, c->npw, c->beta64.as<double2>(), c->npw, src,
                                             c->npw, P, 1, c->nptot, part, part_bytes)) {

@@ -24,7 +24,7 @@ cudaEvent_t take(fs_ctx* c) {
 }  // namespace
 
 ProfScope::ProfScope(fs_ctx* c_, int id_, double bytes, double flops) : c(c_), id(id_) {
-    if (!c->prof.on) return;
+    if (!c || !c->prof.on) return;
     KStat& k = c->prof.st[id];
     k.launches += 1;
     k.bytes += bytes;

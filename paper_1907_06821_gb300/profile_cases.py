@@ -5,6 +5,9 @@
     python -m paper_1907_06821_gb300.profile_cases apply --workload medium --bands 64
     python -m paper_1907_06821_gb300.profile_cases linear --workload medium --nrhs 4 --states 128 --maxit 3000
 
+``wire_local`` is the wire's grid, cutoff and V(r) without projectors: the FFT
+kernels alone, with a few hundred MB on the device (for ncu captures of them).
+
 ``medium`` is a 24 x 24 x 48 bohr box on a 48 x 48 x 96 grid at 20 Ry (41,657
 plane waves) with 64 wells and 8 projectors per atom: operands larger than the
 L2 cache with about 2 GB on the device, for captures that replay a kernel many
@@ -92,7 +95,8 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["apply", "solve", "linear", "chebfd"])
-    ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "medium"])
+    ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "wire_local", "medium"])
+    ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner first (verbose)")
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--repeat", type=int, default=3)
@@ -110,9 +114,15 @@ def main(argv=None):
         w = fi.make_box(L=(24.0, 24.0, 48.0), n=(48, 48, 96), ecut=10.0, natom=64, widths=(0.8, 1.2),
                         lattice=5.0, nstates=128, e_ref=0.05, seed=11, name="medium")
     else:
-        w = fi.make_config(a.workload)
+        w = fi.make_config("wire" if a.workload == "wire_local" else a.workload)
     prec = fs.FS_MIXED if a.precision == "mixed" else fs.FS_FP64
-    ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit, verbose=int(a.verbose))
+    verbose = int(a.verbose or a.autotune)
+    if a.workload == "wire_local":
+        ctx = fs.Context(w.L, w.n, w.ecut, w.k, w.vloc, precision=prec, maxit=a.maxit, verbose=verbose)
+    else:
+        ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit, verbose=verbose)
+    if a.autotune:
+        print("autotune: column tile", ctx.autotune(), flush=True)
     if a.case == "apply":
         dt = torch.complex64 if prec == fs.FS_MIXED else torch.complex128
         X = torch.from_numpy(fi.raw_start_block(a.bands, ctx.npw, 1)).to(dt).cuda()
