@@ -325,6 +325,18 @@ fs_status fs_chebfd(fs_ctx* ctx, double e_ref, double half_width, double emin, d
  * residual vector. */
 fs_status fs_spectral_bounds(fs_ctx* ctx, int iters, double* emin, double* emax);
 
+/* The library's dense FP64 eigensolver (the one its Rayleigh-Ritz steps use): the m
+ * lowest eigenpairs of the Hermitian A (B = NULL) or of the generalized problem
+ * A x = lambda B x with B Hermitian positive definite (Cholesky reduction).  A and B
+ * are HOST arrays, n x n complex128, column-major (1 <= n <= 2048); w receives the m
+ * eigenvalues in ascending order, Z the eigenvectors (n x m, column-major;
+ * orthonormal, or B-orthonormal).  FS_ERR_NUMERIC when B is not positive definite.
+ * Method: Householder reduction to a real tridiagonal matrix, bisection on Sturm
+ * counts, inverse iteration with Gram-Schmidt inside eigenvalue clusters,
+ * back-transformation; Cholesky and triangular solves for B.  (Sec. II.C: the
+ * subspace diagonalisation of the eigensolvers.) */
+fs_status fs_dense_eigh(fs_ctx* ctx, int n, const void* A, const void* B, int m, double* w, void* Z);
+
 /* Failure-path check without a GPU fault: runs the library's bounded device wait (the one
  * the tensor-core pipelines use) on a barrier that nothing completes, polling `polls`
  * times (1 .. 2^24); the wait gives up, raises the context's error flag, and the call

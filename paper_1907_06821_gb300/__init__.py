@@ -127,6 +127,8 @@ def load_library(path: str = LIB_PATH):
     lib.fs_chebfd.restype = ip
     lib.fs_spectral_bounds.argtypes = [vp, ip, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.fs_spectral_bounds.restype = ip
+    lib.fs_dense_eigh.argtypes = [vp, ip, vp, vp, ip, C.POINTER(C.c_double), vp]
+    lib.fs_dense_eigh.restype = ip
     lib.fs_wait_selftest.argtypes = [vp, C.c_longlong]
     lib.fs_wait_selftest.restype = ip
     lib.fs_autotune.argtypes = [vp, C.POINTER(C.c_int)]
@@ -332,6 +334,19 @@ class Context:
         if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
             self._check(st, "fs_linear_solve")
         return out, dict(iters=r.iters, n_hpsi=r.n_hpsi, seconds=r.seconds, err=err[:nrhs].copy(), status=st)
+
+    def dense_eigh(self, A, m=None, B=None):
+        """The m lowest eigenpairs of the Hermitian A (or of A x = lambda B x) by the library's
+        dense FP64 eigensolver; A, B host complex arrays (n x n).  Returns (w, Z [n x m])."""
+        A = np.asfortranarray(A, dtype=np.complex128)
+        n = A.shape[0]
+        m = n if m is None else int(m)
+        Bf = None if B is None else np.asfortranarray(B, dtype=np.complex128)
+        w = np.empty(m, dtype=np.float64)
+        Z = np.empty((n, m), dtype=np.complex128, order="F")
+        self._check(self.lib.fs_dense_eigh(self.h, n, A.ctypes.data, None if Bf is None else Bf.ctypes.data, m,
+                                           _dptr(w), Z.ctypes.data), "fs_dense_eigh")
+        return w, Z
 
     def wait_selftest(self, polls=4096):
         """Run the bounded device wait on a barrier nothing completes; raises FSError

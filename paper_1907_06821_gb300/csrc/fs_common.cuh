@@ -213,6 +213,13 @@ struct Mlp {
 constexpr size_t FS_TABLE_FMT_MAX_BYTES = 32ull << 30;
 constexpr size_t FS_FMT_CHUNK_BYTES = 4ull << 30;
 
+// Workspace of the dense FP64 linear algebra (fs_dense.cu), kept by the context.
+#define FS_DENSE_MAX_N 2048
+struct DenseWork {
+    dbuf V, tau, d, e, e2, Y, z, work, info3, bar, info, T, U, wyG, wyT, wyW, wyW2, gpart;
+    bool attr_set = false;
+};
+
 struct SolverSmall {
     dbuf GA, GB, T1, T2, evals, work, info, theta, act, resid, dots, nrm, shift, dscale, bkin, hres, keep;
     int lwork = 0;
@@ -306,6 +313,7 @@ struct fs_ctx {
 
     Prof prof;
     Mlp mlp;
+    DenseWork dense;
     SolverMem smem;
     dbuf errflag;     // int: set by a device-side wait that gave up
     int gemm_path = 0;
@@ -388,6 +396,15 @@ void mlp_features(fs_ctx* c, const T2* R, const int* act, int na, const double2*
                   float* zt, float* wt);
 template <typename T2> void mlp_make_w(fs_ctx* c, const T2* R, const int* act, int na, T2* W, const double2* dots);
 template <typename T2> void mlp_err_from_proj(fs_ctx* c, const T2* proj, const T2* X, const int* act, int na, T2* E);
+
+// dense FP64 linear algebra (fs_dense.cu); column-major complex, op 0 = N, 1 = C
+void dense_gemm(fs_ctx* c, int opA, int opB, int M, int N, int K, double alpha, const double2* A, int lda,
+                const double2* B, int ldb, double beta, double2* C, int ldc);
+int dense_potrf(fs_ctx* c, int n, double2* A, int lda, double* piv);
+void dense_trsm(fs_ctx* c, int conj, int n, int ncols, const double2* L, int lda, double2* B, int ldb);
+void dense_conj_transpose(fs_ctx* c, int n, int m, const double2* A, int lda, double2* out, int ldo);
+void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int ldz);
+int dense_hegv(fs_ctx* c, int n, double2* GA, double2* GB, int m, double* w);
 
 // solver (fs_solver.cu)
 fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res);

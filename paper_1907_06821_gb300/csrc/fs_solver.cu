@@ -20,8 +20,6 @@
 // FP64 check of the wanted bands, and FP64 iterations only if it fails.
 #include "fs_common.cuh"
 
-#include <cuComplex.h>
-
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -130,15 +128,6 @@ __global__ void gather_sym_kernel(const double2* G, int n, const int* keep, int 
     out[t] = G[keep[i] + (long)keep[j] * n];
 }
 
-// squared diagonal of the Cholesky factor L (k x k) into piv[0..k)
-__global__ void diag_sq_kernel(const double2* L, int k, double* piv) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < k) {
-        double d = L[(long)i * k + i].x;
-        piv[i] = d * d;
-    }
-}
-
 // C (n x m, ld n): row r = U row pos[r] (U k x m, ld k), or 0 where pos[r] < 0
 __global__ void scatter_rows_kernel(double2* C, int n, int m, const double2* U, int k, const int* pos) {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
@@ -186,7 +175,6 @@ struct Solver {
         s.bkin.alloc(nbmax * sizeof(double));
         s.hres.alloc(nbmax * sizeof(double));
         s.evals.alloc(nbmax * sizeof(double));
-        s.info.alloc(sizeof(int));
         s.theta.alloc(nbmax * sizeof(double));
         s.act.alloc(2 * nbmax * sizeof(int));
         s.resid.alloc(nbmax * sizeof(double));
@@ -194,42 +182,23 @@ struct Solver {
         s.nrm.alloc(nbmax * sizeof(double));
         s.shift.alloc(nbmax * sizeof(double));
         s.keep.alloc(2 * nbmax * sizeof(int));
-        int lw1 = 0, lw2 = 0, lw3 = 0, lw4 = 0, meig = 0;
-        FS_SOLVER(cusolverDnZhegvd_bufferSize(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR,
-                                              CUBLAS_FILL_MODE_LOWER, nbmax, s.GA.as<cuDoubleComplex>(), nbmax,
-                                              s.GB.as<cuDoubleComplex>(), nbmax, s.evals.as<double>(), &lw1));
-        FS_SOLVER(cusolverDnZheevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nbmax,
-                                              s.GA.as<cuDoubleComplex>(), nbmax, s.evals.as<double>(), &lw2));
-        FS_SOLVER(cusolverDnZheevdx_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                                               CUBLAS_FILL_MODE_LOWER, nbmax, s.GA.as<cuDoubleComplex>(), nbmax, 0.0,
-                                               0.0, 1, nbmax, &meig, s.evals.as<double>(), &lw3));
-        FS_SOLVER(cusolverDnZpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, nbmax, s.GB.as<cuDoubleComplex>(),
-                                              nbmax, &lw4));
-        s.lwork = std::max(std::max(lw1, lw2), std::max(lw3, lw4));
-        s.work.alloc((size_t)s.lwork * sizeof(cuDoubleComplex));
     }
 
-    // generalized Hermitian eigenproblem GA c = lambda GB c, n x n column-major; returns info
+    // generalized Hermitian eigenproblem GA c = lambda GB c, n x n column-major:
+    // every eigenpair, vectors into GA, values into s.evals; returns the Cholesky info
     int hegvd(int n) {
         ProfScope ps(c, KS_DENSE_LA, 0.0, 0.0);
-        FS_SOLVER(cusolverDnZhegvd(c->solver, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                   s.GA.as<cuDoubleComplex>(), n, s.GB.as<cuDoubleComplex>(), n, s.evals.as<double>(),
-                                   s.work.as<cuDoubleComplex>(), s.lwork, s.info.as<int>()));
-        int info = 0;
-        FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        FS_CUDA(cudaStreamSynchronize(c->stream));
-        return info;
+        return dense_hegv(c, n, s.GA.as<double2>(), s.GB.as<double2>(), n, s.evals.as<double>());
     }
+    // every eigenpair of the Hermitian A (n x n, default s.GA): vectors overwrite A
     int heevd(int n, double2* A = nullptr) {
         if (!A) A = s.GA.as<double2>();
         ProfScope ps(c, KS_DENSE_LA, 0.0, 0.0);
-        FS_SOLVER(cusolverDnZheevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                   (cuDoubleComplex*)A, n, s.evals.as<double>(), s.work.as<cuDoubleComplex>(),
-                                   s.lwork, s.info.as<int>()));
-        int info = 0;
-        FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        FS_CUDA(cudaStreamSynchronize(c->stream));
-        return info;
+        DenseWork& D = c->dense;
+        D.U.ensure((size_t)n * n * sizeof(double2));
+        dense_heev(c, n, A, n, s.evals.as<double>(), D.U.as<double2>(), n);
+        FS_CUDA(cudaMemcpyAsync(A, D.U.p, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+        return 0;
     }
 
     // Rayleigh-Ritz of A on a basis of nb vectors with Gram matrices GA = <S, AS>
@@ -288,16 +257,10 @@ struct Solver {
             gather_sym_kernel<<<nblk((long)k * k), 256, 0, c->stream>>>(s.GB.as<double2>(), nb, kd, k, T2);
             FS_CUDA(cudaGetLastError());
         }
-        FS_SOLVER(cusolverDnZpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)T2, k,
-                                   s.work.as<cuDoubleComplex>(), s.lwork, s.info.as<int>()));
-        diag_sq_kernel<<<nblk(k), 256, 0, c->stream>>>(T2, k, s.nrm.as<double>());
-        FS_CUDA(cudaGetLastError());
-        int info = 0;
+        const int info = dense_potrf(c, k, T2, k, s.nrm.as<double>());  // squared pivots to s.nrm
         piv.resize(k);
-        FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaMemcpyAsync(piv.data(), s.nrm.p, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaStreamSynchronize(c->stream));
-        if (info < 0) throw fs_error(FS_ERR_NUMERIC, "potrf argument error " + std::to_string(info));
         return info;
     }
 
@@ -306,25 +269,17 @@ struct Solver {
     // dropped directions 0) and unscaled.
     int rr_reduced(int nb, const std::vector<int>& keep) {
         const int k = (int)keep.size();
-        cuDoubleComplex* L = s.T2.as<cuDoubleComplex>();
-        cuDoubleComplex* C = s.T1.as<cuDoubleComplex>();
-        const cuDoubleComplex one = make_cuDoubleComplex(1, 0);
+        double2* L = s.T2.as<double2>();
+        double2* C = s.T1.as<double2>();
+        double2* T = s.GA.as<double2>();  // free here: chol_kept copied what it needs into T1
         int info = 0;
         {
             ProfScope ps(c, KS_DENSE_LA, 0.0, 8.0 * k * (double)k * k);
-            FS_BLAS(cublasZtrsm(c->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, CUBLAS_DIAG_NON_UNIT, k,
-                                k, &one, L, k, C, k));
-            FS_BLAS(cublasZtrsm(c->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT,
-                                k, k, &one, L, k, C, k));
-            int meig = 0;
-            FS_SOLVER(cusolverDnZheevdx(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
-                                        CUBLAS_FILL_MODE_LOWER, k, C, k, 0.0, 0.0, 1, m, &meig, s.evals.as<double>(),
-                                        s.work.as<cuDoubleComplex>(), s.lwork, s.info.as<int>()));
-            FS_BLAS(cublasZtrsm(c->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, CUBLAS_DIAG_NON_UNIT, k,
-                                m, &one, L, k, C, k));
-            FS_CUDA(cudaMemcpyAsync(&info, s.info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            FS_CUDA(cudaStreamSynchronize(c->stream));
-            if (info == 0 && meig != m) info = -2;
+            dense_trsm(c, 0, k, k, L, k, C, k);               // L^-1 GA
+            dense_conj_transpose(c, k, k, C, k, T, k);          // GA L^-H
+            dense_trsm(c, 0, k, k, L, k, T, k);               // L^-1 GA L^-H
+            dense_heev(c, k, T, m, s.evals.as<double>(), C, k);  // m lowest pairs, vectors into C
+            dense_trsm(c, 1, k, m, L, k, C, k);               // L^-H V
         }
         if (info != 0) return info;
         double2* GA = s.GA.as<double2>();
@@ -362,22 +317,18 @@ struct Solver {
         if (k < m) return -1;
         double2* T = GB + (long)(nb - k) * nb;  // kept eigenvectors, nb x k
         col_invsqrt_kernel<<<nblk((long)nb * k), 256, 0, c->stream>>>(T, nb, k, s.evals.as<double>() + (nb - k));
-        const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
         double2* tmp = s.T1.as<double2>();
         double2* GAp = s.T2.as<double2>();
         {
         ProfScope ps(c, KS_DENSE_LA, 0.0, 8.0 * nb * (double)nb * k + 8.0 * k * (double)k * nb);
-        FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, k, nb, &one, (cuDoubleComplex*)GA, nb,
-                            (cuDoubleComplex*)T, nb, &zero, (cuDoubleComplex*)tmp, nb));
-        FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_C, CUBLAS_OP_N, k, k, nb, &one, (cuDoubleComplex*)T, nb,
-                            (cuDoubleComplex*)tmp, nb, &zero, (cuDoubleComplex*)GAp, k));
+        dense_gemm(c, 0, 0, nb, k, nb, 1.0, GA, nb, T, nb, 0.0, tmp, nb);
+        dense_gemm(c, 1, 0, k, k, nb, 1.0, T, nb, tmp, nb, 0.0, GAp, k);
         }
         info = heevd(k, GAp);
         if (info != 0) return info;
         {
         ProfScope ps(c, KS_DENSE_LA, 0.0, 8.0 * nb * (double)m * k);
-        FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, nb, m, k, &one, (cuDoubleComplex*)T, nb,
-                            (cuDoubleComplex*)GAp, k, &zero, (cuDoubleComplex*)GA, nb));
+        dense_gemm(c, 0, 0, nb, m, k, 1.0, T, nb, GAp, k, 0.0, GA, nb);
         }
         row_scale_kernel<<<nblk((long)nb * m), 256, 0, c->stream>>>(GA, nb, m, s.dscale.as<double>());
         FS_CUDA(cudaGetLastError());
