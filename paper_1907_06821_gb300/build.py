@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), sources()))
     tmp = LIB + ".tmp"
-    cmd = [nvcc_path(), "-shared", "-o", tmp] + objs + ARCH + ["-lcusolver", "-lcublas", "-lcudart"]
+    cmd = [nvcc_path(), "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -243,10 +243,6 @@ fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const d
             FS_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
             c->own_stream = true;
         }
-        FS_SOLVER(cusolverDnCreate(&c->solver));
-        FS_SOLVER(cusolverDnSetStream(c->solver, c->stream));
-        FS_BLAS(cublasCreate(&c->blas));
-        FS_BLAS(cublasSetStream(c->blas, c->stream));
         build_sphere(c);
         ctx_prepare_fft(c);
         upload_potential(c, vloc);
@@ -345,8 +341,6 @@ void fs_destroy(fs_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     prof_release(c);
-    if (c->solver) cusolverDnDestroy(c->solver);
-    if (c->blas) cublasDestroy(c->blas);
     cudaStream_t s = c->stream;
     bool own = c->own_stream;
     delete c;

@@ -16,12 +16,11 @@
 // residual vector (the estimate used to place Chebyshev filters).
 #include "fs_common.cuh"
 
-#include <cuComplex.h>
-
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <numeric>
+#include <vector>
 
 namespace {
 
@@ -107,40 +106,66 @@ double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, i
     return 0.5 * (lo + hi);
 }
 
-double znrm2(fs_ctx* c, long n, const double2* x) {
-    double r = 0;
-    FS_BLAS(cublasDznrm2(c->blas, (int)n, (const cuDoubleComplex*)x, 1, &r));
-    return r;
+// Re sum conj(x) y over n entries: per-block partial sums in a fixed order,
+// added on the host in block order (deterministic)
+constexpr int DOT_BLOCKS = 256;
+__global__ void dot_re_kernel(const double2* __restrict__ x, const double2* __restrict__ y, long n, double* part) {
+    __shared__ double sh[CT];
+    double s = 0;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        s += x[t].x * y[t].x + x[t].y * y[t].y;
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = CT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// y += a x
+__global__ void axpy_kernel(long n, double a, const double2* __restrict__ x, double2* __restrict__ y) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        y[t] = make_double2(y[t].x + a * x[t].x, y[t].y + a * x[t].y);
+}
+
+// x *= a
+__global__ void scal_kernel(long n, double a, double2* __restrict__ x) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n; t += (long)gridDim.x * blockDim.x)
+        x[t] = make_double2(a * x[t].x, a * x[t].y);
 }
 
 double zdot_re(fs_ctx* c, long n, const double2* x, const double2* y) {
-    cuDoubleComplex r;
-    FS_BLAS(cublasZdotc(c->blas, (int)n, (const cuDoubleComplex*)x, 1, (const cuDoubleComplex*)y, 1, &r));
-    return cuCreal(r);
+    dbuf& part = c->dense.gpart;
+    part.ensure(DOT_BLOCKS * sizeof(double));
+    dot_re_kernel<<<DOT_BLOCKS, CT, 0, c->stream>>>(x, y, n, part.as<double>());
+    FS_CUDA(cudaGetLastError());
+    std::vector<double> h(DOT_BLOCKS);
+    FS_CUDA(cudaMemcpyAsync(h.data(), part.p, DOT_BLOCKS * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    double s = 0;
+    for (double v : h) s += v;
+    return s;
 }
 
+double znrm2(fs_ctx* c, long n, const double2* x) { return std::sqrt(std::max(0.0, zdot_re(c, n, x, x))); }
+
 void zaxpy(fs_ctx* c, long n, double a, const double2* x, double2* y) {
-    const cuDoubleComplex al = make_cuDoubleComplex(a, 0);
-    FS_BLAS(cublasZaxpy(c->blas, (int)n, &al, (const cuDoubleComplex*)x, 1, (cuDoubleComplex*)y, 1));
+    axpy_kernel<<<cblocks(n), CT, 0, c->stream>>>(n, a, x, y);
+    FS_CUDA(cudaGetLastError());
 }
 
 void zscal(fs_ctx* c, long n, double a, double2* x) {
-    FS_BLAS(cublasZdscal(c->blas, (int)n, &a, (cuDoubleComplex*)x, 1));
+    scal_kernel<<<cblocks(n), CT, 0, c->stream>>>(n, a, x);
+    FS_CUDA(cudaGetLastError());
 }
 
-// Hermitian eigendecomposition of the n x n matrix A (column-major, in place): eigenvalues to w (device)
-void heevd(fs_ctx* c, int n, double2* A, double* w, dbuf& work, dbuf& info) {
-    int lw = 0;
-    FS_SOLVER(cusolverDnZheevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
-                                          (cuDoubleComplex*)A, n, w, &lw));
-    work.ensure((size_t)std::max(lw, 1) * sizeof(cuDoubleComplex));
-    info.ensure(sizeof(int));
-    FS_SOLVER(cusolverDnZheevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, (cuDoubleComplex*)A, n,
-                               w, work.as<cuDoubleComplex>(), lw, info.as<int>()));
-    int h = 0;
-    FS_CUDA(cudaMemcpyAsync(&h, info.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    FS_CUDA(cudaStreamSynchronize(c->stream));
-    if (h != 0) throw fs_error(FS_ERR_NUMERIC, "ChebFD: eigensolve failed (info " + std::to_string(h) + ")");
+// every eigenpair of the Hermitian n x n matrix A (column-major): vectors overwrite A, values to w (device)
+void heevd(fs_ctx* c, int n, double2* A, double* w) {
+    dbuf& Z = c->dense.U;
+    Z.ensure((size_t)n * n * sizeof(double2));
+    dense_heev(c, n, A, n, w, Z.as<double2>(), n);
+    FS_CUDA(cudaMemcpyAsync(A, Z.p, (size_t)n * n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
 }
 
 }  // namespace
@@ -182,7 +207,7 @@ fs_status chebfd_impl(fs_ctx* c, double e_ref, double d, double emin, double ema
     const double cc = 0.5 * (emax + emin), e = 0.5 * (emax - emin);
     const std::vector<double> coef = window_coefficients((e_ref - d - cc) / e, (e_ref + d - cc) / e, degree);
     const size_t vb = (size_t)nvec * npw * sizeof(double2);
-    dbuf X, Tp, Tc, HT, Y, small, small2, evals, work, info;
+    dbuf X, Tp, Tc, HT, Y, small, small2, evals;
     for (dbuf* q : {&X, &Tp, &Tc, &HT, &Y}) q->alloc(vb);
     small.alloc((size_t)nvec * nvec * sizeof(double2));
     small2.alloc((size_t)nvec * nvec * sizeof(double2));
@@ -226,7 +251,7 @@ fs_status chebfd_impl(fs_ctx* c, double e_ref, double d, double emin, double ema
         std::vector<double> lam(m);
         {
             ProfScope ps(c, KS_DENSE_LA, 0.0, 0.0);
-            heevd(c, m, GB, evals.as<double>(), work, info);
+            heevd(c, m, GB, evals.as<double>());
         }
         FS_CUDA(cudaMemcpyAsync(lam.data(), evals.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaStreamSynchronize(c->stream));
@@ -236,19 +261,15 @@ fs_status chebfd_impl(fs_ctx* c, double e_ref, double d, double emin, double ema
         double2* T = GB + (long)(m - k) * m;  // kept eigenvectors, m x k
         col_rsqrt_kernel<<<(int)(((long)m * k + 255) / 256), 256, 0, c->stream>>>(T, m, k, evals.as<double>() + (m - k));
         FS_CUDA(cudaGetLastError());
-        const cuDoubleComplex one = make_cuDoubleComplex(1, 0), zero = make_cuDoubleComplex(0, 0);
         double2* tmp = small3.as<double2>();
         double2* Ar = GA;  // reuse after the product: A_r = T^H GA T into small3 then back
         {
             ProfScope ps(c, KS_DENSE_LA, 0.0, 16.0 * (double)m * m * k);
-            FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, k, m, &one, (cuDoubleComplex*)GA, m,
-                                (cuDoubleComplex*)T, m, &zero, (cuDoubleComplex*)tmp, m));
-            FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_C, CUBLAS_OP_N, k, k, m, &one, (cuDoubleComplex*)T, m,
-                                (cuDoubleComplex*)tmp, m, &zero, (cuDoubleComplex*)Ar, k));
-            heevd(c, k, Ar, evals.as<double>(), work, info);
+            dense_gemm(c, 0, 0, m, k, m, 1.0, GA, m, T, m, 0.0, tmp, m);
+            dense_gemm(c, 1, 0, k, k, m, 1.0, T, m, tmp, m, 0.0, Ar, k);
+            heevd(c, k, Ar, evals.as<double>());
             // coefficients C = T V (m x k) into tmp
-            FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, m, k, k, &one, (cuDoubleComplex*)T, m,
-                                (cuDoubleComplex*)Ar, k, &zero, (cuDoubleComplex*)tmp, m));
+            dense_gemm(c, 0, 0, m, k, k, 1.0, T, m, Ar, k, 0.0, tmp, m);
         }
         eps_h.assign(k, 0.0);
         FS_CUDA(cudaMemcpyAsync(eps_h.data(), evals.p, k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

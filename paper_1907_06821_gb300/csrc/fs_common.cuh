@@ -2,8 +2,6 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 
 #include <cstdint>
 #include <string>
@@ -72,22 +70,6 @@ __host__ __device__ inline int geo_slot(const LineGeo& g, int p) { return p + (g
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess) {                                                         \
             throw fs_error(FS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-        }                                                                                \
-    } while (0)
-
-#define FS_BLAS(call)                                                                    \
-    do {                                                                                 \
-        cublasStatus_t s_ = (call);                                                      \
-        if (s_ != CUBLAS_STATUS_SUCCESS) {                                               \
-            throw fs_error(FS_ERR_CUDA, std::string(#call) + ": cublas status " + std::to_string((int)s_)); \
-        }                                                                                \
-    } while (0)
-
-#define FS_SOLVER(call)                                                                  \
-    do {                                                                                 \
-        cusolverStatus_t s_ = (call);                                                    \
-        if (s_ != CUSOLVER_STATUS_SUCCESS) {                                             \
-            throw fs_error(FS_ERR_CUDA, std::string(#call) + ": cusolver status " + std::to_string((int)s_)); \
         }                                                                                \
     } while (0)
 
@@ -248,8 +230,6 @@ struct fs_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;   // the device that was current at fs_create (every buffer lives there)
-    cusolverDnHandle_t solver = nullptr;
-    cublasHandle_t blas = nullptr;
 
     // basis tables (device)
     dbuf col_start;   // int [ncol+1]

@@ -1,7 +1,8 @@
 // Small dense FP64 linear algebra of the Rayleigh-Ritz steps, on the GPU.
 //
 // Matrices are complex double, column-major, leading dimension = rows.
-//   dense_gemm   C = alpha op(A) op(B) + beta C, op = N or C (conjugate transpose),
+//   dense_gemm   C = alpha op(A) op(B) + beta C, op = N, C (conjugate transpose) or,
+//                for B, T (transpose);
 //                32 x 32 tiles staged in shared memory (FP64 FMA).
 //   dense_potrf  Cholesky A = L L^H of the lower triangle, blocked (32): the
 //                diagonal block factorised in shared memory, the panel by a
@@ -41,7 +42,7 @@ constexpr long long BAR_LIMIT = 1ll << 22;
 __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
 
 // ------------------------------------------------------------------ GEMM
-// C[M x N] = alpha op(A) op(B) + beta C; opA/opB: 0 = N, 1 = C (conjugate transpose)
+// C[M x N] = alpha op(A) op(B) + beta C; opA/opB: 0 = N, 1 = C (conjugate transpose), opB 2 = T
 // Split K (gridDim.z > 1): block z takes k in [z kc, min(K, (z + 1) kc)) and
 // writes its partial product to C + z M N (ld M) with alpha = 1, beta = 0.
 __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA, int opB, double alpha,
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA
         const int k0 = blockIdx.z * kc;
         K = min(K - k0, kc);
         A += opA == 0 ? (long)k0 * lda : k0;
-        B += opB == 0 ? k0 : (long)k0 * ldb;
+        B += opB == 0 ? k0 : (long)k0 * ldb;  // C and T read B[n + k ldb]
         C += (size_t)blockIdx.z * M * N;
         ldc = M;
     }
@@ -82,7 +83,10 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA
             const int gn = n0 + nn;
             const int gk2 = k0 + kk;
             v = make_double2(0.0, 0.0);
-            if (gn < N && gk2 < K) v = opB == 0 ? B[gk2 + (long)gn * ldb] : zconj(B[gn + (long)gk2 * ldb]);
+            if (gn < N && gk2 < K) {
+                v = opB == 0 ? B[gk2 + (long)gn * ldb] : B[gn + (long)gk2 * ldb];
+                if (opB == 1) v = zconj(v);
+            }
             Bs[kk][nn] = v;
         }
         __syncthreads();

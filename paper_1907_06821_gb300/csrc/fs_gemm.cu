@@ -10,7 +10,6 @@
 //               rotations, projector application).
 #include "fs_common.cuh"
 
-#include <cuComplex.h>
 
 #include <algorithm>
 
@@ -199,13 +198,12 @@ void gemm_gram(fs_ctx* c, int M, int N, int K, const T2* A, long lda, const int*
     ProfScope ps(c, ks_prec<T2>(kid), ((double)M + N) * K * sizeof(T2) + (double)M * N * sizeof(double2),
                  8.0 * M * N * K);
     if constexpr (sizeof(T2) == 16) {
-        // FP64 without row maps and with C column-major is a plain ZGEMM, C = alpha A^H B + beta C
-        // (A, B column-major K x M and K x N): cuBLAS, whose FP64 rate on this part is about
-        // three times that of the CUDA-core kernel below
+        // FP64 without row maps and with C column-major is a plain GEMM, C = alpha A^H B + beta C
+        // (A, B column-major K x M and K x N): the dense FP64 GEMM (split K when the output is
+        // small), about three times the rate of the row-mapped kernel below
         if (!amap && !bmap && ci == 1) {
-            const cuDoubleComplex al = make_cuDoubleComplex(alpha, 0), be = make_cuDoubleComplex(beta, 0);
-            FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_C, CUBLAS_OP_N, M, N, K, &al, (const cuDoubleComplex*)A, (int)lda,
-                                (const cuDoubleComplex*)B, (int)ldb, &be, (cuDoubleComplex*)C, (int)cj));
+            dense_gemm(c, 1, 0, M, N, K, alpha, (const double2*)A, (int)lda, (const double2*)B, (int)ldb, beta, C,
+                       (int)cj);
             return;
         }
     }
@@ -239,12 +237,10 @@ void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, cons
                  8.0 * M * N * K);
     if constexpr (sizeof(T2) == 16 && sizeof(A2) == 16) {
         // FP64 without row maps, D aliasing C (or beta = 0) and a unit stride in the coefficients
-        // is a plain ZGEMM on the column-major views: C (N x M) = B (N x K) op(Acoef) (K x M)
+        // is a plain GEMM on the column-major views: C (N x M) = B (N x K) op(Acoef) (K x M)
         if (!bmap && !cmap && (beta == 0.0 || (D == C && ldd == ldc)) && (ak == 1 || ai == 1)) {
-            const cuDoubleComplex al = make_cuDoubleComplex(alpha, 0), be = make_cuDoubleComplex(beta, 0);
-            FS_BLAS(cublasZgemm(c->blas, CUBLAS_OP_N, ak == 1 ? CUBLAS_OP_N : CUBLAS_OP_T, N, M, K, &al,
-                                (const cuDoubleComplex*)B, (int)ldb, (const cuDoubleComplex*)A,
-                                (int)(ak == 1 ? ai : ak), &be, (cuDoubleComplex*)C, (int)ldc));
+            dense_gemm(c, 0, ak == 1 ? 0 : 2, N, M, K, alpha, (const double2*)B, (int)ldb, (const double2*)A,
+                       (int)(ak == 1 ? ai : ak), beta, (double2*)C, (int)ldc);
             return;
         }
     }

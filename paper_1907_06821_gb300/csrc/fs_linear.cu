@@ -14,7 +14,6 @@
 // converged one is frozen (step length zero).
 #include "fs_common.cuh"
 
-#include <cuComplex.h>
 
 #include <algorithm>
 #include <chrono>
