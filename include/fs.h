@@ -168,6 +168,16 @@ fs_status fs_set_initial_states(fs_ctx* ctx, const void* psi, int n, int damp, i
  * stays usable after any of these. */
 fs_status fs_solve(fs_ctx* ctx, double e_ref, int nstates, double tol, fs_result* res);
 
+/* The nstates lowest eigenpairs of H to residual tol (Ha): the all-band
+ * conjugate-gradient minimisation of the ground-state codes the paper builds
+ * on (Sec. II.A-B, PEtot and LS3DF), in the same locally optimal block form as
+ * fs_solve but on H itself (Rayleigh quotients <s_i, H s_j>, residual
+ * H x - theta x, one H application per band per iteration, preconditioner
+ * 1 / (1 + |q|^2/2)), with the same precision ladder (opts.precision) and
+ * guard bands.  Results ordered by eigenvalue; fs_get_states returns the
+ * states.  Return codes as fs_solve. */
+fs_status fs_solve_lowest(fs_ctx* ctx, int nstates, double tol, fs_result* res);
+
 /* Copy the n first states of the last solve (in the order of res->eps), or of
  * the last fs_chebfd (in the order of its eps), [n][npw] complex128, to host or
  * device memory. */
@@ -324,6 +334,20 @@ fs_status fs_chebfd(fs_ctx* ctx, double e_ref, double half_width, double emin, d
  * extreme eigenvalues of the tridiagonal matrix widened by the norm of the last
  * residual vector. */
 fs_status fs_spectral_bounds(fs_ctx* ctx, int iters, double* emin, double* emax);
+
+/* Wave-function interpolation between two k-points (Sec. II.D): from orthonormal
+ * eigenpairs of k1 (n1 states) and k2 (n2 >= n1 states), H(k) = alpha H(k1) +
+ * (1 - alpha) H(k2) in the basis psi_i(k1) is
+ *     H_ij = alpha eps1_i delta_ij + (1 - alpha) sum_m U*_im U_jm eps2_m,
+ * U the rows of S_il = <psi_l(k2)|psi_i(k1)> made orthonormal by Gram-Schmidt in
+ * index order (U = L^-1 S, S S^H = L L^H); its eigenvalues (ascending) go to eps
+ * (host [n1]) and the states psi_q = alpha sum_j C_jq psi_j(k1) + (1 - alpha)
+ * sum_{j,l} C_jq U_jl psi_l(k2) to psi.  psi1 [n1][npw], psi2 [n2][npw] and psi
+ * [n1][npw] are DEVICE arrays of complex128 on one common set of npw plane waves
+ * (the context's sphere: periodic parts of the states of both k-points); eps1,
+ * eps2 are host arrays.  FS_ERR_NUMERIC when S has dependent rows. */
+fs_status fs_kinterp(fs_ctx* ctx, double alpha, int n1, const double* eps1, const void* psi1, int n2,
+                     const double* eps2, const void* psi2, double* eps, void* psi);
 
 /* The library's dense FP64 eigensolver (the one its Rayleigh-Ritz steps use): the m
  * lowest eigenpairs of the Hermitian A (B = NULL) or of the generalized problem

@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH):
     lib.fs_set_initial_states.restype = ip
     lib.fs_solve.argtypes = [vp, dp, ip, dp, C.POINTER(fs_result)]
     lib.fs_solve.restype = ip
+    lib.fs_solve_lowest.argtypes = [vp, ip, dp, C.POINTER(fs_result)]
+    lib.fs_solve_lowest.restype = ip
     lib.fs_get_states.argtypes = [vp, vp, ip, ip]
     lib.fs_get_states.restype = ip
     lib.fs_apply_H_static.argtypes = [vp, vp, vp, ip, dp]
@@ -127,6 +129,9 @@ def load_library(path: str = LIB_PATH):
     lib.fs_chebfd.restype = ip
     lib.fs_spectral_bounds.argtypes = [vp, ip, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     lib.fs_spectral_bounds.restype = ip
+    lib.fs_kinterp.argtypes = [vp, dp, ip, C.POINTER(C.c_double), vp, ip, C.POINTER(C.c_double), vp,
+                               C.POINTER(C.c_double), vp]
+    lib.fs_kinterp.restype = ip
     lib.fs_dense_eigh.argtypes = [vp, ip, vp, vp, ip, C.POINTER(C.c_double), vp]
     lib.fs_dense_eigh.restype = ip
     lib.fs_wait_selftest.argtypes = [vp, C.c_longlong]
@@ -270,6 +275,19 @@ class Context:
         return dict(eps=eps, resid=res, nconv=r.nconv, iters=r.iters, iters_mixed=r.iters_mixed,
                     n_hpsi=r.n_hpsi, seconds=r.seconds, status=st)
 
+    def solve_lowest(self, nstates, tol=1e-6, allow_unconverged=False):
+        """The nstates lowest eigenpairs of H (fs_solve_lowest); eps ascending."""
+        eps = np.zeros(nstates)
+        res = np.zeros(nstates)
+        r = fs_result()
+        r.eps = _dptr(eps)
+        r.resid = _dptr(res)
+        st = self.lib.fs_solve_lowest(self.h, int(nstates), float(tol), C.byref(r))
+        if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
+            self._check(st, "fs_solve_lowest")
+        return dict(eps=eps, resid=res, nconv=r.nconv, iters=r.iters, iters_mixed=r.iters_mixed,
+                    n_hpsi=r.n_hpsi, seconds=r.seconds, status=st)
+
     def get_states(self, n, device=False, out=None):
         """The n states nearest E [n][npw] complex128: a numpy array, a CUDA tensor
         (device=True), or written into `out` (a contiguous complex128 tensor, host or
@@ -334,6 +352,20 @@ class Context:
         if st not in (FS_OK, FS_ERR_NOT_CONVERGED) or (st == FS_ERR_NOT_CONVERGED and not allow_unconverged):
             self._check(st, "fs_linear_solve")
         return out, dict(iters=r.iters, n_hpsi=r.n_hpsi, seconds=r.seconds, err=err[:nrhs].copy(), status=st)
+
+    def kinterp(self, alpha, eps1, psi1, eps2, psi2):
+        """Interpolated eigenpairs at alpha (fs_kinterp); psi1 [n1][npw], psi2 [n2][npw] CUDA
+        complex128 tensors, eps1/eps2 host arrays.  Returns (eps [n1], psi CUDA [n1][npw])."""
+        import torch
+        n1, n2 = psi1.shape[0], psi2.shape[0]
+        e1 = np.ascontiguousarray(eps1, dtype=np.float64)
+        e2 = np.ascontiguousarray(eps2, dtype=np.float64)
+        eps = np.empty(n1)
+        out = torch.empty((n1, self.npw), dtype=torch.complex128, device=psi1.device)
+        self._check(self.lib.fs_kinterp(self.h, float(alpha), n1, _dptr(e1), C.c_void_p(psi1.data_ptr()), n2,
+                                        _dptr(e2), C.c_void_p(psi2.data_ptr()), _dptr(eps),
+                                        C.c_void_p(out.data_ptr())), "fs_kinterp")
+        return eps, out
 
     def dense_eigh(self, A, m=None, B=None):
         """The m lowest eigenpairs of the Hermitian A (or of A x = lambda B x) by the library's

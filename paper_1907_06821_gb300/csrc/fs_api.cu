@@ -322,6 +322,17 @@ fs_status fs_solve(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* 
     return g != FS_OK ? g : st;
 }
 
+fs_status fs_solve_lowest(fs_ctx* c, int nstates, double tol, fs_result* res) {
+    if (!c) return FS_ERR_ARG;
+    if (!res || !res->eps || !res->resid || nstates <= 0 || !(tol > 0)) {
+        c->err = "fs_solve_lowest: bad arguments";
+        return FS_ERR_ARG;
+    }
+    fs_status st = FS_OK;
+    fs_status g = guarded(c, [&] { st = solve_impl(c, 0.0, nstates, tol, res, true); });
+    return g != FS_OK ? g : st;
+}
+
 fs_status fs_get_states(fs_ctx* c, void* psi, int n, int where) {
     if (!c) return FS_ERR_ARG;
     if (n < 0 || n > c->nresult || (n > 0 && !psi) || (where != FS_HOST && where != FS_DEVICE)) {

@@ -387,4 +387,4 @@ void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int 
 int dense_hegv(fs_ctx* c, int n, double2* GA, double2* GB, int m, double* w);
 
 // solver (fs_solver.cu)
-fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res);
+fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res, bool lowest = false);

@@ -18,6 +18,12 @@
 // Mixed precision: vectors, FFTs and GEMMs in FP32 (tensor-core TF32 x3),
 // dense algebra in FP64, Y (and YP) recomputed every 10 iterations; then an
 // FP64 check of the wanted bands, and FP64 iterations only if it fails.
+//
+// Lowest-state mode (the all-band CG of the ground-state codes the paper
+// builds on): the same block iteration on H itself, Y = H X, Rayleigh
+// quotients <s_i, H s_j>, residual R = Y - theta X (one H application per
+// band per iteration, half of the folded form), preconditioner
+// 1 / (1 + |q|^2 / 2), results ordered by eigenvalue.
 #include "fs_common.cuh"
 
 #include <algorithm>
@@ -158,6 +164,7 @@ struct Solver {
     explicit Solver(fs_ctx* c_) : c(c_), s(c_->smem.small) {}
     long long n_hpsi = 0;
     int verbose = 0;
+    bool lowest = false;  // lowest eigenpairs of H instead of the pairs nearest E
 
     template <typename T2> void HE(const T2* in, T2* out, int nb, const int* map = nullptr) {
         apply_H_impl<T2>(c, in, out, nb, E, map);
@@ -366,7 +373,8 @@ struct Solver {
         ensure_small(3 * m);
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
-        gemm_gram<T2>(c, m, m, c->npw, Y, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
+        // folded: <s_i, A s_j> = <(H-E) s_i, (H-E) s_j>; lowest: <s_i, H s_j>
+        gemm_gram<T2>(c, m, m, c->npw, lowest ? X : Y, c->npw, nullptr, Y, c->npw, nullptr, GA, 1, m, 1.0, 0.0);
         gemm_gram<T2>(c, m, m, c->npw, X, c->npw, nullptr, X, c->npw, nullptr, GB, 1, m, 1.0, 0.0);
         {
             // a non-finite start block (or H image) is reported before a dense eigensolve sees it:
@@ -424,11 +432,16 @@ struct Solver {
         hres_h.resize(m);
         FS_CUDA(cudaMemcpyAsync(hres_h.data(), s.hres.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         vec_rh<T2>(c, X, Y, s.dots.as<double2>(), m, RH);
-        HE(RH, ZR, m);
-        vec_a_resid<T2>(c, ZR, RH, X, s.dots.as<double2>(), s.theta.as<double>(), m, s.resid.as<double>());
         ra.resize(m);
         th.resize(m);
-        FS_CUDA(cudaMemcpyAsync(ra.data(), s.resid.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        if (lowest) {
+            // the H residual y - <x, y> x is the residual of the lowest-state iteration
+            FS_CUDA(cudaMemcpyAsync(ra.data(), s.hres.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        } else {
+            HE(RH, ZR, m);
+            vec_a_resid<T2>(c, ZR, RH, X, s.dots.as<double2>(), s.theta.as<double>(), m, s.resid.as<double>());
+            FS_CUDA(cudaMemcpyAsync(ra.data(), s.resid.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        }
         FS_CUDA(cudaMemcpyAsync(th.data(), s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         FS_CUDA(cudaStreamSynchronize(c->stream));
         ctx_check_errflag(c);
@@ -438,7 +451,9 @@ struct Solver {
     // Threshold on the A residual matching an H residual of about tol: for an
     // isolated eigenvector at distance d = sqrt(theta) from E the A residual is
     // about 2 d times the H residual (factor floored at 1e-3).
-    double tol_a(double theta, double target) const { return target * std::max(std::sqrt(std::max(theta, 0.0)), 1e-3); }
+    double tol_a(double theta, double target) const {
+        return lowest ? target : target * std::max(std::sqrt(std::max(theta, 0.0)), 1e-3);
+    }
 
     // Rayleigh-Ritz on H within the wanted A-Ritz vectors (the nstates lowest
     // theta plus bands tied with the nstates-th within 1e-3): H-Ritz pairs and
@@ -449,7 +464,8 @@ struct Solver {
     void h_ritz(Blocks<T2>& B, const std::vector<double>& th, int& n, std::vector<double>& eps,
                 std::vector<double>& res, std::vector<int>& order) {
         n = nstates;
-        while (n < m && th[n] <= th[nstates - 1] * (1.0 + 1e-3)) ++n;
+        const double tie = lowest ? 1e-3 * std::max(1.0, std::fabs(th[nstates - 1])) : 1e-3 * th[nstates - 1];
+        while (n < m && th[n] <= th[nstates - 1] + tie) ++n;
         T2* X = B.X.template as<T2>();
         T2* Y = B.Y.template as<T2>();
         double2* GA = s.GA.as<double2>();
@@ -477,6 +493,7 @@ struct Solver {
         order.resize(n);
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (lowest) return eps[a] < eps[b];
             double da = std::fabs(eps[a] - E), db = std::fabs(eps[b] - E);
             if (da != db) return da < db;
             return eps[a] < eps[b];
@@ -525,9 +542,11 @@ struct Solver {
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
         // W = M R on the active bands, made orthogonal to X and normalised
-        if (c->mlp.record) record_pairs<T2>(B, act_h);
+        if (c->mlp.record && !lowest) record_pairs<T2>(B, act_h);
         const bool teter = c->opt.precond == FS_PREC_TETER;
-        if (c->opt.precond == FS_PREC_LEARNED) {
+        if (lowest) {
+            vec_make_w<T2>(c, B.RH.template as<T2>(), act, na, W, 0.0, 1.0, 2, nullptr);
+        } else if (c->opt.precond == FS_PREC_LEARNED) {
             mlp_make_w<T2>(c, B.RH.template as<T2>(), act, na, W, s.dots.as<double2>());
         } else {
             if (teter) vec_band_kin<T2>(c, X, m, s.bkin.as<double>());
@@ -559,7 +578,7 @@ struct Solver {
             int nb = m + na + (useP ? na : 0);
             // <s_i, A s_j> = <(H-E)s_i, (H-E)s_j>: the Y images keep the small
             // Rayleigh quotients of A accurate in the FP32 stage
-            gram_blocks<T2>(GA, nb, SY, SY, maps, sizes, offs, nblk);
+            gram_blocks<T2>(GA, nb, lowest ? S : SY, SY, maps, sizes, offs, nblk);
             gram_blocks<T2>(GB, nb, S, S, maps, sizes, offs, nblk);
             int info = rr_basis(nb, true, tau_for<T2>(), piv_for<T2>());
             if (info != 0) {
@@ -665,10 +684,11 @@ struct Solver {
 
 }  // namespace
 
-fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res) {
+fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result* res, bool lowest) {
     auto t0 = std::chrono::steady_clock::now();
     Solver S(c);
-    S.E = e_ref;
+    S.lowest = lowest;
+    S.E = lowest ? 0.0 : e_ref;
     S.nstates = nstates;
     S.tol = tol;
     S.verbose = c->opt.verbose;
@@ -678,7 +698,7 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
     if (m > c->npw) throw fs_error(FS_ERR_ARG, "nstates + guard exceeds the number of plane waves");
     S.ensure_small(3 * m);
     const long npw = c->npw;
-    if (c->opt.precond == FS_PREC_LEARNED || c->mlp.record) {
+    if (!lowest && (c->opt.precond == FS_PREC_LEARNED || c->mlp.record)) {
         mlp_setup(c);
         if (c->mlp.e_ref != e_ref || !c->mlp.Mdev.p) {
             c->mlp.e_ref = e_ref;
@@ -729,7 +749,8 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
             FS_CUDA(cudaMemcpyAsync(th.data(), S.s.theta.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
             FS_CUDA(cudaStreamSynchronize(c->stream));
             int nw = nstates;
-            while (nw < m && th[nw] <= th[nstates - 1] * (1.0 + 1e-3)) ++nw;
+            const double tie = lowest ? 1e-3 * std::max(1.0, std::fabs(th[nstates - 1])) : 1e-3 * th[nstates - 1];
+            while (nw < m && th[nw] <= th[nstates - 1] + tie) ++nw;
             S.HE(B64.X.as<double2>(), B64.Y.as<double2>(), nw);
             S.h_ritz<double2>(B64, th, nres, eps, resid, order);
             done = true;

@@ -144,6 +144,8 @@ __global__ void make_w_kernel(const T2* __restrict__ R, const int* __restrict__ 
             double num = 27.0 + xx * (18.0 + xx * (12.0 + 8.0 * xx));
             double kk = num / (num + 16.0 * xx * xx * xx * xx);
             m = kk * kk / (tk * tk);
+        } else if (precond == 2) {  // lowest states of H itself: 1 / (1 + |q|^2 / 2)
+            m = 1.0 / (1.0 + kin[g]);
         } else {
             double d = kin[g] - e_ref;
             m = 1.0 / (d * d + dE2);
