@@ -198,7 +198,7 @@ constexpr size_t FS_FMT_CHUNK_BYTES = 4ull << 30;
 // Workspace of the dense FP64 linear algebra (fs_dense.cu), kept by the context.
 #define FS_DENSE_MAX_N 2048
 struct DenseWork {
-    dbuf V, tau, d, e, e2, Y, z, work, info3, bar, info, T, U, wyG, wyT, wyW, wyW2, gpart;
+    dbuf V, tau, d, e, e2, Y, z, work, info3, bar, info, T, U, wyG, wyT, wyW, wyW2, gpart, qrG, qrT;
     bool attr_set = false;
 };
 

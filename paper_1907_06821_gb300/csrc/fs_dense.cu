@@ -19,10 +19,10 @@
 //        counts come from the leading minors, rescaled, without division);
 //     3. eigenvectors of T by inverse iteration (Gaussian elimination with
 //        partial pivoting on T - lambda I), vectors of eigenvalues closer
-//        than 1e-6 ||T|| handled as one cluster and made orthogonal to each
-//        other by modified Gram-Schmidt;
+//        than 1e-10 ||T|| handled as one cluster and made orthogonal to each
+//        other by modified Gram-Schmidt (a warp per cluster);
 //     4. back-transformation Z = Q z in blocks of 32 reflectors (compact WY
-//        form), each block as three GEMMs.
+//        form), each block as three GEMMs, then one Cholesky QR pass on Z.
 // Every device-side wait (the grid barrier) is bounded: on expiry the
 // context's error flag is raised and the kernel returns.
 #include "fs_common.cuh"
@@ -66,30 +66,48 @@ __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
-    for (int k0 = 0; k0 < K; k0 += TK) {
+    // tile element e (0 .. 511) of op(A) and op(B) for the k step at k0; the next step's
+    // elements are loaded into registers while the current step's are multiplied
+    auto load = [&](int k0, double2 (&va)[2], double2 (&vb)[2]) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
-            const int e = t + u * 256;  // 0 .. 511 = TK x TB
+            const int e = t + u * 256;
             // op(A)(m, k): N -> A[m + k lda] (m fastest), C -> conj(A[k + m lda]) (k fastest)
             int mm, kk;
             if (opA == 0) { mm = e & (TB - 1); kk = e >> 5; } else { kk = e & (TK - 1); mm = e >> 4; }
             const int gm = m0 + mm, gk = k0 + kk;
             double2 v = make_double2(0.0, 0.0);
             if (gm < M && gk < K) v = opA == 0 ? A[gm + (long)gk * lda] : zconj(A[gk + (long)gm * lda]);
-            As[kk][mm] = v;
-            // op(B)(k, n): N -> B[k + n ldb] (k fastest), C -> conj(B[n + k ldb]) (n fastest)
+            va[u] = v;
+            // op(B)(k, n): N -> B[k + n ldb] (k fastest), C and T -> B[n + k ldb] (n fastest)
             int nn;
             if (opB == 0) { kk = e & (TK - 1); nn = e >> 4; } else { nn = e & (TB - 1); kk = e >> 5; }
-            const int gn = n0 + nn;
-            const int gk2 = k0 + kk;
+            const int gn = n0 + nn, gk2 = k0 + kk;
             v = make_double2(0.0, 0.0);
             if (gn < N && gk2 < K) {
                 v = opB == 0 ? B[gk2 + (long)gn * ldb] : B[gn + (long)gk2 * ldb];
                 if (opB == 1) v = zconj(v);
             }
-            Bs[kk][nn] = v;
+            vb[u] = v;
         }
+    };
+    auto store = [&](const double2 (&va)[2], const double2 (&vb)[2]) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int e = t + u * 256;
+            int mm, kk, nn;
+            if (opA == 0) { mm = e & (TB - 1); kk = e >> 5; } else { kk = e & (TK - 1); mm = e >> 4; }
+            As[kk][mm] = va[u];
+            if (opB == 0) { kk = e & (TK - 1); nn = e >> 4; } else { nn = e & (TB - 1); kk = e >> 5; }
+            Bs[kk][nn] = vb[u];
+        }
+    };
+    double2 va[2], vb[2];
+    if (K > 0) load(0, va, vb);
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        store(va, vb);
         __syncthreads();
+        if (k0 + TK < K) load(k0 + TK, va, vb);
 #pragma unroll
         for (int kk = 0; kk < TK; ++kk) {
             const double2 a0 = As[kk][tx], a1 = As[kk][tx + 16];
@@ -533,21 +551,27 @@ __global__ void tri_bisect_kernel(const double* d, const double* e2, int n, int 
 }
 
 // ------------------------------------------------------------------ tridiagonal eigenvectors
-// Inverse iteration for the clusters of w (ascending): thread k starts a
-// cluster when w[k] - w[k - 1] > 1e-6 ||T|| and computes its vectors in order,
-// each orthogonalised against the cluster's earlier ones.  z: [n][m] real
-// (position-major, so that a warp's threads touch consecutive words), work:
-// [n][5][m] elimination factors.
+// Inverse iteration for the clusters of w (ascending), one warp per index: the
+// warp of index k0 starts a cluster when w[k0] - w[k0 - 1] > 1e-10 ||T|| and
+// computes the cluster's vectors in order, each made orthogonal to the
+// cluster's earlier ones.  An eigenvector from inverse iteration is accurate
+// to about eps ||T|| / gap, so vectors outside a cluster are orthogonal to
+// 1e-6 or better; eigenvalues closer than that (the E +- d pairs of the folded
+// spectrum, an orthonormal block's unit eigenvalues) share a cluster.  Lane 0
+// runs the elimination and the substitutions (sequential in the position),
+// all lanes the Gram-Schmidt steps and the norms.  z: [n][m] real
+// (position-major), work: [n][5][m] elimination factors.
 __global__ void tri_invit_kernel(const double* d, const double* e, int n, int m, const double* w,
                                  const double* info3, double* z, double* work) {
-    const int k0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (k0 >= m) return;
     const double tnorm = fmax(info3[3], 1e-300);
-    const double ctol = 1e-6 * tnorm;
-    if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;  // not a cluster start
+    const double ctol = 1e-10 * tnorm;
+    if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;  // not a cluster start (warp-uniform)
     int k1 = k0 + 1;
     while (k1 < m && w[k1] - w[k1 - 1] <= ctol) ++k1;
-    // factor f of position i for this thread: work[(i * 5 + f) * m + k0]
+    // factor f of position i for this cluster: work[(i * 5 + f) * m + k0]
 #define WK(f, i) work[((long)(i) * 5 + (f)) * m + k0]
 #define ZV(q, i) z[(long)(i) * m + (q)]
     const double sep = 10.0 * DBL_EPSILON * tnorm;
@@ -556,70 +580,79 @@ __global__ void tri_invit_kernel(const double* d, const double* e, int n, int m,
         double lam = w[k];
         if (lam - lam_prev < sep) lam = lam_prev + sep;  // separate equal eigenvalues of a cluster
         lam_prev = lam;
-        // elimination with partial pivoting of T - lam I: U rows (u0, u1, u2), multipliers, swaps
-        double p0 = d[0] - lam, p1 = n > 1 ? e[0] : 0.0, p2 = 0.0;
-        for (int i = 0; i < n - 1; ++i) {
-            const double s = e[i], a = d[i + 1] - lam, t = i + 1 < n - 1 ? e[i + 1] : 0.0;
-            if (fabs(p0) >= fabs(s)) {
-                if (p0 == 0.0) p0 = sep;
-                const double mu = s / p0;
-                WK(0, i) = p0; WK(1, i) = p1; WK(2, i) = p2; WK(3, i) = mu; WK(4, i) = 0.0;
-                p0 = a - mu * p1;
-                p1 = t - mu * p2;
-                p2 = 0.0;
-            } else {
-                const double mu = p0 / s;
-                WK(0, i) = s; WK(1, i) = a; WK(2, i) = t; WK(3, i) = mu; WK(4, i) = 1.0;
-                p0 = p1 - mu * a;
-                p1 = p2 - mu * t;
-                p2 = 0.0;
-            }
-        }
-        WK(0, n - 1) = p0 == 0.0 ? sep : p0;
-        for (int i = 0; i < n - 1; ++i) {
-            const double u = WK(0, i);
-            if (fabs(u) < sep) WK(0, i) = u < 0 ? -sep : sep;
-        }
-        // start vector: a fixed pseudo-random sequence per index
-        unsigned int st = 2654435761u * (unsigned int)(k + 1) + 12345u;
-        for (int i = 0; i < n; ++i) {
-            st = st * 1664525u + 1013904223u;
-            ZV(k, i) = 0.5 + (double)(st >> 8) * (1.0 / 16777216.0);
-        }
-        for (int it = 0; it < 4; ++it) {
-            // forward: apply the row operations
-            double xi = ZV(k, 0);
+        if (lane == 0) {
+            // elimination with partial pivoting of T - lam I: U rows (u0, u1, u2), multipliers, swaps
+            double p0 = d[0] - lam, p1 = n > 1 ? e[0] : 0.0, p2 = 0.0;
             for (int i = 0; i < n - 1; ++i) {
-                const double xn = ZV(k, i + 1);
-                if (WK(4, i) != 0.0) {
-                    ZV(k, i) = xn;
-                    xi = xi - WK(3, i) * xn;
+                const double s = e[i], a = d[i + 1] - lam, t = i + 1 < n - 1 ? e[i + 1] : 0.0;
+                if (fabs(p0) >= fabs(s)) {
+                    if (p0 == 0.0) p0 = sep;
+                    const double mu = s / p0;
+                    WK(0, i) = p0; WK(1, i) = p1; WK(2, i) = p2; WK(3, i) = mu; WK(4, i) = 0.0;
+                    p0 = a - mu * p1;
+                    p1 = t - mu * p2;
+                    p2 = 0.0;
                 } else {
-                    ZV(k, i) = xi;
-                    xi = xn - WK(3, i) * xi;
+                    const double mu = p0 / s;
+                    WK(0, i) = s; WK(1, i) = a; WK(2, i) = t; WK(3, i) = mu; WK(4, i) = 1.0;
+                    p0 = p1 - mu * a;
+                    p1 = p2 - mu * t;
+                    p2 = 0.0;
                 }
             }
-            ZV(k, n - 1) = xi;
-            // back substitution with the three diagonals of U
-            double x2 = 0.0, x1 = ZV(k, n - 1) / WK(0, n - 1);
-            ZV(k, n - 1) = x1;
-            for (int i = n - 2; i >= 0; --i) {
-                const double x0 = (ZV(k, i) - WK(1, i) * x1 - WK(2, i) * x2) / WK(0, i);
-                ZV(k, i) = x0;
-                x2 = x1;
-                x1 = x0;
+            WK(0, n - 1) = p0 == 0.0 ? sep : p0;
+            for (int i = 0; i < n - 1; ++i) {
+                const double u = WK(0, i);
+                if (fabs(u) < sep) WK(0, i) = u < 0 ? -sep : sep;
             }
-            // orthogonalise against the cluster's earlier vectors, normalise
+            // start vector: a fixed pseudo-random sequence per index
+            unsigned int st = 2654435761u * (unsigned int)(k + 1) + 12345u;
+            for (int i = 0; i < n; ++i) {
+                st = st * 1664525u + 1013904223u;
+                ZV(k, i) = 0.5 + (double)(st >> 8) * (1.0 / 16777216.0);
+            }
+        }
+        __syncwarp();
+        for (int it = 0; it < 4; ++it) {
+            if (lane == 0) {
+                // forward: apply the row operations
+                double xi = ZV(k, 0);
+                for (int i = 0; i < n - 1; ++i) {
+                    const double xn = ZV(k, i + 1);
+                    if (WK(4, i) != 0.0) {
+                        ZV(k, i) = xn;
+                        xi = xi - WK(3, i) * xn;
+                    } else {
+                        ZV(k, i) = xi;
+                        xi = xn - WK(3, i) * xi;
+                    }
+                }
+                ZV(k, n - 1) = xi;
+                // back substitution with the three diagonals of U
+                double x2 = 0.0, x1 = ZV(k, n - 1) / WK(0, n - 1);
+                ZV(k, n - 1) = x1;
+                for (int i = n - 2; i >= 0; --i) {
+                    const double x0 = (ZV(k, i) - WK(1, i) * x1 - WK(2, i) * x2) / WK(0, i);
+                    ZV(k, i) = x0;
+                    x2 = x1;
+                    x1 = x0;
+                }
+            }
+            __syncwarp();
+            // orthogonalise against the cluster's earlier vectors (warp-parallel), normalise
             for (int q = k0; q < k; ++q) {
                 double dot = 0;
-                for (int i = 0; i < n; ++i) dot += ZV(q, i) * ZV(k, i);
-                for (int i = 0; i < n; ++i) ZV(k, i) -= dot * ZV(q, i);
+                for (int i = lane; i < n; i += 32) dot += ZV(q, i) * ZV(k, i);
+                for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+                for (int i = lane; i < n; i += 32) ZV(k, i) -= dot * ZV(q, i);
+                __syncwarp();
             }
             double nrm = 0;
-            for (int i = 0; i < n; ++i) nrm += ZV(k, i) * ZV(k, i);
-            nrm = sqrt(nrm);
-            const double inv = nrm > 0 ? 1.0 / nrm : 1.0;
-            for (int i = 0; i < n; ++i) ZV(k, i) *= inv;
+            for (int i = lane; i < n; i += 32) nrm += ZV(k, i) * ZV(k, i);
+            for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+            const double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 1.0;
+            for (int i = lane; i < n; i += 32) ZV(k, i) *= inv;
+            __syncwarp();
         }
     }
 #undef WK
@@ -837,7 +870,7 @@ void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int 
                                               D.info3.as<double>());
     tri_bisect_kernel<<<m, 32, 0, c->stream>>>(D.d.as<double>(), D.e2.as<double>(), n, m,
                                                                       D.info3.as<double>(), w);
-    tri_invit_kernel<<<cdiv(m, 64), 64, 0, c->stream>>>(D.d.as<double>(), D.e.as<double>(), n, m, w,
+    tri_invit_kernel<<<cdiv((long)m * 32, 128), 128, 0, c->stream>>>(D.d.as<double>(), D.e.as<double>(), n, m, w,
                                                         D.info3.as<double>(), D.z.as<double>(), D.work.as<double>());
     tri_z_to_Z_kernel<<<cdiv((long)n * m, 256), 256, 0, c->stream>>>(n, m, D.z.as<double>(), Z, ldz);
     FS_CUDA(cudaGetLastError());
@@ -860,6 +893,22 @@ void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int 
             dense_gemm(c, 0, 0, rows, m, nbk, -1.0, Vb, n, W2, nbk, 1.0, Z + r0, ldz);
         }
         FS_CUDA(cudaGetLastError());
+    }
+    // one Cholesky QR pass: the vectors of eigenvalues outside a common cluster are orthogonal
+    // only to about eps ||T|| / gap; their Gram matrix is I + O(that), so Z <- Z L^-H with
+    // Z^H Z = L L^H restores orthonormality to working precision (it mixes only nearly
+    // degenerate vectors)
+    if (m > 1) {
+        D.qrG.ensure((size_t)m * m * sizeof(double2));
+        D.qrT.ensure((size_t)m * n * sizeof(double2));
+        double2* G = D.qrG.as<double2>();
+        double2* T = D.qrT.as<double2>();
+        dense_gemm(c, 1, 0, m, m, n, 1.0, Z, ldz, Z, ldz, 0.0, G, m);
+        if (dense_potrf(c, m, G, m, nullptr) == 0) {
+            dense_conj_transpose(c, n, m, Z, ldz, T, m);
+            dense_trsm(c, 0, m, n, G, m, T, m);
+            dense_conj_transpose(c, m, n, T, m, Z, ldz);
+        }
     }
     ctx_check_errflag(c);
 }

@@ -39,7 +39,10 @@ def test_gpu_arm_line_assembly():
     stats["nonlocal_project"]["ms"] = 5000.0
     args = types.SimpleNamespace(precision="mixed", no_cpu=True, no_fp64=True, steps=1, warmup=3, workload="wire")
     w = types.SimpleNamespace(n=(72, 72, 144), natom=256, nproj=8, nstates=256, e_ref=0.03, nbands=272)
-    ctx = types.SimpleNamespace(npw=193673)
+    gv = np.zeros((193673, 3), dtype=np.int32)
+    gv[:, 0] = np.arange(193673) % 57                                # 57 x 45 distinct (g0, g1) columns
+    gv[:, 1] = (np.arange(193673) // 57) % 45
+    ctx = types.SimpleNamespace(npw=193673, gvectors=lambda: gv)
     r = [dict(nconv=256, iters=125, iters_mixed=125, n_hpsi=75600, resid=np.zeros(256), status=0)]
     clocks = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
     d = bench.make_line(args, w, ctx, r, stats, 256, 31.0, 32.0, 256, clocks, 6793.4, 1980.5, "measured", 1,
@@ -53,4 +56,8 @@ def test_gpu_arm_line_assembly():
     assert roof["traffic"] is not None                          # an ncu ratio exists for this kernel
     assert d["e2e"]["h2d_bytes_per_step"] == 272 * 10 * 16
     assert d["gpu_launches"] == sum(v["launches"] for v in stats.values())
+    hs = d["hpsi_survey"]
+    bands = stats["col_inverse_fft"]["bytes"] / ((193673 + 144 * 57 * 45) * 8.0)
+    assert abs(hs["bands"] - bands) <= 1e-9 * bands
+    assert hs["bytes_per_band"] == 2 * 193673 * 8 + 8 * 72 * 72 * 144 * 8
     json.dumps(d)

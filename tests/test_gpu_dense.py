@@ -81,3 +81,14 @@ def test_generalized_rejects_indefinite_b(ctx):
     with pytest.raises(fs.FSError) as ei:
         c.dense_eigh(A, 5, B=B)
     assert ei.value.code == fs.FS_ERR_NUMERIC and "column 8" in str(ei.value)
+
+
+def test_heev_near_identity_cluster(ctx):
+    """The scaled overlap of an orthonormal block: every eigenvalue within 1e-9 of 1,
+    one cluster of 300; the vectors must still come out orthonormal."""
+    fs, c = ctx
+    A = np.eye(300) + 1e-9 * _herm(300, 12)
+    w, Z = c.dense_eigh(A, 300)
+    assert np.abs(w - np.linalg.eigvalsh(A)).max() <= 1e-14
+    assert np.abs(Z.conj().T @ Z - np.eye(300)).max() <= 1e-10
+    assert np.linalg.norm(A @ Z - Z * w[None, :], axis=0).max() <= 1e-13
