@@ -96,7 +96,15 @@ typedef struct {
     int verbose;               /* > 0: one line per iteration on stderr */
     int gemm_path;             /* FP32-stage GEMMs: FS_GEMM_TENSOR (default, tcgen05 TF32 x3 split)
                                   or FS_GEMM_CUDA_CORES (FP32 FMA); FP64 work always uses FP64 FMA */
+    int projectors;            /* FS_PROJ_AUTO (0, default): the projector table beta[N_p][npw] is
+                                  stored when its FP64 form takes at most 16 GB, else generated;
+                                  FS_PROJ_STORED; FS_PROJ_GENERATED: beta is formed where it is used
+                                  from per-type radial factors and per-atom one-axis phase tables
+                                  (beta = f_c(|q|) exp(-i q_x X_a) exp(-i q_y Y_a) exp(-i q_z Z_a)), so
+                                  no N_p x npw table exists (fs_apply_H_static then refuses) */
 } fs_options;
+
+enum { FS_PROJ_AUTO = 0, FS_PROJ_STORED = 1, FS_PROJ_GENERATED = 2 };
 
 typedef struct {
     int nconv;                 /* states among the nstates wanted with resid <= tol */

@@ -35,6 +35,7 @@ nonlocal    : projector norm -> 1 at large cutoff (Parseval); numerical FT of th
               real-space Gaussians; one projector -> secular equation roots
 full H      : Hermitian; matrix-free apply == dense apply; spectrum invariant
               under a grid translation of wells and atoms together
+chunked     : the nonlocal term applied atom chunk by atom chunk equals the stored-table apply
 """
 
 
@@ -77,28 +78,41 @@ def vtilde(vloc):
     return np.fft.fftn(vloc) / vloc.size
 
 
-def beta_matrix(w, g, q):
-    """B[G, a*nproj + c] = beta_{a,c}(q_G) (complex128, (N, natom*nproj))."""
+def beta_matrix(w, g, q, atoms=None):
+    """B[G, a*nproj + c] = beta_{a,c}(q_G) (complex128, (N, natom*nproj)); with
+    `atoms`, only the columns of those atoms (in that order)."""
     L = w.L
     omega = float(np.prod(L))
     q2 = np.sum(q * q, axis=1)
+    # the factor of each projector type without the atom's phase
+    shapes = []
+    for (l, ax, wid) in w.proj:
+        ns = (np.pi * wid * wid) ** (-0.75)
+        radial = omega ** -0.5 * ns * (2.0 * np.pi * wid * wid) ** 1.5 \
+            * np.exp(-0.5 * wid * wid * q2)
+        if l == 0:
+            f = radial.astype(np.complex128)
+        elif l == 1:
+            f = radial * (np.sqrt(2.0) / wid) * (-1j * wid * wid * q[:, ax])
+        else:
+            raise ValueError("only s and p projectors")
+        shapes.append(f)
     cols = []
-    for a in range(w.natom):
+    for a in (range(w.natom) if atoms is None else atoms):
         phase = np.exp(-1j * (q @ w.pos[a]))
-        for (l, ax, wid) in w.proj:
-            ns = (np.pi * wid * wid) ** (-0.75)
-            radial = omega ** -0.5 * ns * (2.0 * np.pi * wid * wid) ** 1.5 \
-                * np.exp(-0.5 * wid * wid * q2)
-            if l == 0:
-                f = radial.astype(np.complex128)
-            elif l == 1:
-                f = radial * (np.sqrt(2.0) / wid) * (-1j * wid * wid * q[:, ax])
-            else:
-                raise ValueError("only s and p projectors")
+        for f in shapes:
             cols.append(f * phase)
     if not cols:
         return np.zeros((q.shape[0], 0), dtype=np.complex128)
     return np.stack(cols, axis=1)
+
+
+def _at_origin(w):
+    """The workload with one atom at the origin (its projectors without a phase)."""
+    import copy
+    w0 = copy.copy(w)
+    w0.pos = np.zeros((1, 3))
+    return w0
 
 
 def block_D(w):
@@ -129,17 +143,25 @@ def dense_H(w, include=("T", "V", "NL")):
 
 
 class Hamiltonian:
-    """Matrix-free H (and H - s) on the sphere, FP64, via numpy.fft."""
+    """Matrix-free H (and H - s) on the sphere, FP64, via numpy.fft.
 
-    def __init__(self, w):
+    The projector table B (N x natom*nproj) is stored when it takes at most
+    table_bytes (default 16 GB); otherwise the nonlocal term is applied atom
+    chunk by atom chunk from the same beta_matrix, never holding all of B."""
+
+    def __init__(self, w, table_bytes=16e9, atom_chunk=128):
         self.w = w
         self.g, self.q = sphere(w.L, w.n, w.ecut, w.k)
         self.npw = self.g.shape[0]
         self.kin = kinetic(self.q)
         n = np.asarray(w.n)
         self.gi = tuple((self.g % n[None, :]).T)
-        self.B = beta_matrix(w, self.g, self.q) if w.nproj > 0 else None
-        self.Dfull = block_D(w) if w.nproj > 0 else None
+        self.atom_chunk = atom_chunk
+        store = w.nproj > 0 and self.npw * w.natom * w.nproj * 16 <= table_bytes
+        self.B = beta_matrix(w, self.g, self.q) if store else None
+        self.Dfull = block_D(w) if store else None
+        self.chunked = w.nproj > 0 and not store
+        self.F = None
         self.napply = 0
 
     def apply(self, X, shift=0.0):
@@ -156,6 +178,24 @@ class Hamiltonian:
         if self.B is not None:
             P = self.B.conj().T @ X.T                 # <beta|psi>, (Np, nband)
             out += (self.B @ (self.Dfull @ P)).T
+        elif self.chunked:
+            # beta_{a,c}(q) = f_c(q) e^{-i q.R_a}: the projections and the sum over the
+            # projectors, atom chunk by atom chunk, with the phases of the chunk's atoms
+            # E[G, a] = e^{-i q_G.R_a} (f_c = the type factors, beta_matrix with no phase)
+            w = self.w
+            if self.F is None:
+                self.F = beta_matrix(_at_origin(w), self.g, self.q, [0]).T  # (nproj, N)
+            nb = X.shape[0]
+            U = [np.conj(self.F) * X[b][None, :] for b in range(nb)]         # (nproj, N) per band
+            acc = np.zeros((nb, w.nproj, X.shape[1]), dtype=np.complex128)   # sum_a E Q per type
+            for a0 in range(0, w.natom, self.atom_chunk):
+                atoms = list(range(a0, min(w.natom, a0 + self.atom_chunk)))
+                E = np.exp(-1j * (self.q @ w.pos[atoms].T))                  # (N, na)
+                for b in range(nb):
+                    P = (U[b] @ np.conj(E)).T                                # <beta_ac|psi_b>, (na, nproj)
+                    Q = np.matmul(w.D[atoms], P[:, :, None])[:, :, 0]        # D_a P_a
+                    acc[b] += (E @ Q).T
+            out += np.sum(self.F[None, :, :] * acc, axis=1)                  # sum_c f_c sum_a E Q
         self.napply += X.shape[0]
         return out
 

@@ -22,6 +22,7 @@ FS_FP64, FS_MIXED = 0, 1
 FS_PREC_M, FS_PREC_TETER, FS_PREC_LEARNED = 0, 1, 2
 FS_HOST, FS_DEVICE = 0, 1
 FS_GEMM_TENSOR, FS_GEMM_CUDA_CORES = 0, 1
+FS_PROJ_AUTO, FS_PROJ_STORED, FS_PROJ_GENERATED = 0, 1, 2
 
 STATUS_NAMES = {0: "FS_OK", 1: "FS_ERR_ARG", 2: "FS_ERR_GRID_TOO_SMALL", 3: "FS_ERR_OOM",
                 4: "FS_ERR_CUDA", 5: "FS_ERR_NUMERIC", 6: "FS_ERR_NOT_CONVERGED",
@@ -41,7 +42,8 @@ class fs_projectors(C.Structure):
 class fs_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("dE", C.c_double),
                 ("maxit", C.c_int), ("guard", C.c_int), ("seed", C.c_ulonglong),
-                ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("gemm_path", C.c_int)]
+                ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("gemm_path", C.c_int),
+                ("projectors", C.c_int)]
 
 
 class fs_result(C.Structure):
@@ -173,7 +175,7 @@ class Context:
 
     def __init__(self, L, n, ecut, k, vloc, pos=None, proj=(), D=None, precision=FS_FP64,
                  precond=FS_PREC_M, dE=0.5, maxit=5000, guard=-1, seed=1, stream=None, verbose=0,
-                 gemm_path=FS_GEMM_TENSOR):
+                 gemm_path=FS_GEMM_TENSOR, projectors=0):
         self.lib = load_library()
         self._keep = []
         g = fs_grid((C.c_double * 3)(*[float(x) for x in L]), (C.c_int * 3)(*[int(x) for x in n]))
@@ -193,7 +195,7 @@ class Context:
             pr.natom, pr.nproj = posa.shape[0], len(proj)
             pr.pos, pr.l, pr.axis, pr.width, pr.D = _dptr(posa), _iptr(la), _iptr(axa), _dptr(wa), _dptr(Da)
         opt = fs_options(precision, precond, dE, maxit, guard, seed,
-                         C.c_void_p(stream) if stream else None, verbose, gemm_path)
+                         C.c_void_p(stream) if stream else None, verbose, gemm_path, projectors)
         self.precision = precision
         h = C.c_void_p()
         st = self.lib.fs_create(C.byref(g), float(ecut), _dptr(kk), _dptr(v), C.byref(pr), C.byref(opt),

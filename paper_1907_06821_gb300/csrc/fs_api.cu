@@ -168,8 +168,19 @@ void build_projectors(fs_ctx* c, const fs_projectors* pr) {
     FS_CUDA(cudaMemcpy(dl.p, pr->l, c->nproj * sizeof(int), cudaMemcpyHostToDevice));
     FS_CUDA(cudaMemcpy(dax.p, pr->axis, c->nproj * sizeof(int), cudaMemcpyHostToDevice));
     FS_CUDA(cudaMemcpy(dw.p, pr->width, c->nproj * sizeof(double), cudaMemcpyHostToDevice));
-    c->beta64.alloc((size_t)c->nptot * c->npw * sizeof(double2));
     const double omega = c->L[0] * c->L[1] * c->L[2];
+    const double table_bytes = (double)c->nptot * c->npw * sizeof(double2);
+    c->beta_gen = c->opt.projectors == FS_PROJ_GENERATED ||
+                  (c->opt.projectors == FS_PROJ_AUTO && table_bytes > 16e9);
+    if (c->beta_gen) {
+        beta_gen_setup(c, pr, omega);
+        const size_t nd = (size_t)c->natom * c->nproj * c->nproj;
+        c->Dmat.alloc(nd * sizeof(double));
+        FS_CUDA(cudaMemcpy(c->Dmat.p, pr->D, nd * sizeof(double), cudaMemcpyHostToDevice));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        return;
+    }
+    c->beta64.alloc((size_t)c->nptot * c->npw * sizeof(double2));
     dim3 g((unsigned)std::min<long>(256, (c->npw + 255) / 256), c->nptot);
     beta_kernel<<<g, 256, 0, c->stream>>>(c->beta64.as<double2>(), dmil.as<int>(), c->npw, 2.0 * M_PI / c->L[0],
                                           2.0 * M_PI / c->L[1], 2.0 * M_PI / c->L[2], c->k[0], c->k[1], c->k[2],
@@ -183,7 +194,7 @@ void build_projectors(fs_ctx* c, const fs_projectors* pr) {
 }
 
 void ensure_fp32_tables(fs_ctx* c) {
-    if (c->nptot > 0 && !c->beta32.p) {
+    if (c->nptot > 0 && !c->beta_gen && !c->beta32.p) {
         size_t cnt = (size_t)c->nptot * c->npw;
         c->beta32.alloc(cnt * sizeof(float2));
         vec_convert<double2, float2>(c, c->beta64.as<double2>(), c->beta32.as<float2>(), cnt);
@@ -231,6 +242,8 @@ fs_status fs_create(const fs_grid* grid, double ecut, const double k[3], const d
         if (c->opt.maxit <= 0) c->opt.maxit = 5000;
         if (c->opt.precision != FS_FP64 && c->opt.precision != FS_MIXED) throw fs_error(FS_ERR_ARG, "bad precision");
         if (c->opt.precond < FS_PREC_M || c->opt.precond > FS_PREC_LEARNED) throw fs_error(FS_ERR_ARG, "bad precond");
+        if (c->opt.projectors < FS_PROJ_AUTO || c->opt.projectors > FS_PROJ_GENERATED)
+            throw fs_error(FS_ERR_ARG, "bad projectors mode");
         if (c->opt.gemm_path != FS_GEMM_TENSOR && c->opt.gemm_path != FS_GEMM_CUDA_CORES)
             throw fs_error(FS_ERR_ARG, "bad gemm_path");
         c->gemm_path = c->opt.gemm_path;

@@ -259,6 +259,10 @@ struct fs_ctx {
     size_t hchunk_bytes = 96ull << 20;  // column-buffer bytes per band chunk (kept in L2 between passes)
 
     // projectors
+    bool beta_gen = false;  // no table: projector values formed where they are used (fs_beta.cuh)
+    dbuf bg_rad, bg_ph, bg_rad32, bg_ph32, bg_gidx, bg_pl;
+    int bg_span = 0;
+    dbuf beta_chunk;  // generated rows of the table for the CUDA-core GEMMs
     dbuf beta64;      // double2 [nptot][npw]
     dbuf beta32;      // float2  [nptot][npw]
     dbuf Dmat;        // double  [natom][nproj][nproj]
@@ -336,13 +340,20 @@ template <typename T2, typename A2>
 void gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const T2* B, long ldb, const int* bmap,
              T2* C, long ldc, const int* cmap, double alpha, double beta, const T2* D, long ldd, int kid = KS_ROTATE);
 
-// tensor-core GEMMs for the FP32 stage (fs_tc.cu)
+// tensor-core GEMMs for the FP32 stage (fs_tc.cu); gen: the table operand (A of the
+// Gram form, B of the apply form) is the generated projector table (fs_beta.cuh)
+struct BetaGen;
 void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, const int* amap, const float2* B,
-                  long ldb, const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid);
+                  long ldb, const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid,
+                  const BetaGen* gen = nullptr);
 template <typename A2>
 void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const float2* B, long ldb,
                 const int* bmap, float2* C, long ldc, const int* cmap, double alpha, double beta, const float2* D,
-                long ldd, int kid);
+                long ldd, int kid, const BetaGen* gen = nullptr);
+// generated projectors (fs_beta.cu)
+void beta_gen_setup(fs_ctx* c, const fs_projectors* pr, double omega);
+template <typename T2> void beta_project_chunked(fs_ctx* c, const T2* psi, const int* rowmap, int nb, double2* P);
+template <typename T2> void beta_add_chunked(fs_ctx* c, const double2* Q, int nb, T2* hpsi);
 int* ctx_errflag(fs_ctx* c);
 void ctx_check_errflag(fs_ctx* c);
 

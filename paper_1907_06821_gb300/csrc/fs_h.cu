@@ -11,6 +11,7 @@
 //   3. col_forward : forward FFT along z, scale by 1/N, pick the sphere
 //                    entries and add (|q|^2/2 - shift) psi.
 // Nonlocal part: P = B^H psi (Gram GEMM), Q = D P per atom, hpsi += B Q.
+#include "fs_beta.cuh"
 #include "fs_common.cuh"
 #include "fs_fft.cuh"
 
@@ -691,8 +692,19 @@ void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, cons
         c->projbuf.ensure((size_t)nb * c->nptot * sizeof(double2));
         c->projbuf2.ensure((size_t)nb * c->nptot * sizeof(double2));
         double2* P = c->projbuf.as<double2>();
-        gemm_gram<T2>(c, c->nptot, nb, c->npw, beta_of<T2>(c), c->npw, nullptr, psi, c->npw, rowmap, P, 1,
-                      c->nptot, 1.0, 0.0, ks_prec<T2>(KS_NL_PROJ));
+        bool tc_gen = false;
+        if constexpr (sizeof(T2) == 8) tc_gen = c->beta_gen && c->gemm_path == FS_GEMM_TENSOR;
+        const BetaGen gen = c->beta_gen ? beta_gen_of(c) : BetaGen{};
+        if (tc_gen) {
+            if constexpr (sizeof(T2) == 8)
+                tc_gemm_gram(c, c->nptot, nb, c->npw, nullptr, 0, nullptr, psi, c->npw, rowmap, P, 1, c->nptot, 1.0,
+                             0.0, KS_NL_PROJ, &gen);
+        } else if (c->beta_gen) {
+            beta_project_chunked<T2>(c, psi, rowmap, nb, P);
+        } else {
+            gemm_gram<T2>(c, c->nptot, nb, c->npw, beta_of<T2>(c), c->npw, nullptr, psi, c->npw, rowmap, P, 1,
+                          c->nptot, 1.0, 0.0, ks_prec<T2>(KS_NL_PROJ));
+        }
         double2* Q = c->projbuf2.as<double2>();
         int blocks = (int)std::min<long>(4096, ((long)nb * c->nptot + 255) / 256);
         {
@@ -701,8 +713,16 @@ void apply_H_impl(fs_ctx* c, const T2* psi, T2* hpsi, int nb, double shift, cons
         }
         FS_CUDA(cudaGetLastError());
         // hpsi[b][g] += sum_p Q[b][p] beta[p][g]
-        gemm_nn<T2, double2>(c, nb, c->npw, c->nptot, Q, c->nptot, 1, beta_of<T2>(c), c->npw, nullptr, hpsi,
-                             c->npw, nullptr, 1.0, 1.0, hpsi, c->npw, ks_prec<T2>(KS_NL_ADD));
+        if (tc_gen) {
+            if constexpr (sizeof(T2) == 8)
+                tc_gemm_nn<double2>(c, nb, c->npw, c->nptot, Q, c->nptot, 1, nullptr, c->npw, nullptr, hpsi, c->npw,
+                                    nullptr, 1.0, 1.0, hpsi, c->npw, KS_NL_ADD, &gen);
+        } else if (c->beta_gen) {
+            beta_add_chunked<T2>(c, Q, nb, hpsi);
+        } else {
+            gemm_nn<T2, double2>(c, nb, c->npw, c->nptot, Q, c->nptot, 1, beta_of<T2>(c), c->npw, nullptr, hpsi,
+                                 c->npw, nullptr, 1.0, 1.0, hpsi, c->npw, ks_prec<T2>(KS_NL_ADD));
+        }
     }
 }
 
@@ -768,6 +788,11 @@ extern "C" fs_status fs_apply_H_static(fs_ctx* c, const void* psi, void* hpsi, i
         return FS_ERR_ARG;
     }
     if (nband == 0) return FS_OK;
+    if (c->beta_gen) {
+        c->err = "fs_apply_H_static: the context generates its projectors (no stored table); create it with "
+                 "projectors = FS_PROJ_STORED";
+        return FS_ERR_ARG;
+    }
     void* base = nullptr;
     fs_status st = scratch_address(c->device, &base, c->err);
     if (st != FS_OK) return st;

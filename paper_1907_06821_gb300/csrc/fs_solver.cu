@@ -43,9 +43,13 @@ template <typename T2> struct Blocks {
     explicit Blocks(dbuf* d)
         : X(d[0]), Y(d[1]), W(d[2]), YW(d[3]), P(d[4]), YP(d[5]), RH(d[6]), ZR(d[7]), tX(d[8]), tY(d[9]), tP(d[10]),
           tYP(d[11]) {}
-    void alloc(int m, long npw) {
+    // full = false: only X, Y and the rotation targets tX, tY (what the FP64 check
+    // of an FP32 result uses); the rest is allocated when FP64 iterations start
+    void alloc(int m, long npw, bool full = true) {
         size_t b = (size_t)m * npw * sizeof(T2);
-        for (dbuf* d : {&X, &Y, &W, &YW, &P, &YP, &RH, &ZR, &tX, &tY, &tP, &tYP}) d->ensure(b);
+        for (dbuf* d : {&X, &Y, &tX, &tY}) d->ensure(b);
+        if (full)
+            for (dbuf* d : {&W, &YW, &P, &YP, &RH, &ZR, &tP, &tYP}) d->ensure(b);
         haveP = false;
     }
 };
@@ -729,7 +733,7 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         B32.alloc(m, npw);
         vec_convert<double2, float2>(c, x0.as<double2>(), B32.X.as<float2>(), (size_t)m * npw);
         S.init_block<float2>(B32);
-        B64.alloc(m, npw);
+        B64.alloc(m, npw, false);
         // FP32 stage to a margin below tol (its residuals carry FP32 noise), then
         // an FP64 check of the wanted bands: Y = (H-E)X in FP64 for those bands
         // only, Rayleigh-Ritz on H with the FP64 overlap, FP64 residuals.  A
@@ -766,6 +770,7 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
                                 c->stream));
     }
     if (!done) {
+        B64.alloc(m, npw);
         S.init_block<double2>(B64);
         status = S.run<double2>(B64, std::max(0, c->opt.maxit - iters), tol, false, iters, 0, eps, resid, order, nres);
     }

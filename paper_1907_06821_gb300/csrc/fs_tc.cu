@@ -24,6 +24,7 @@
 // Every mbarrier wait is bounded; on expiry the kernel raises the context's
 // error flag, waits (bounded) for its copies and MMAs in flight, releases
 // tensor memory and returns.
+#include "fs_beta.cuh"
 #include "fs_common.cuh"
 
 #include <algorithm>
@@ -479,6 +480,58 @@ __global__ void fmt_rot_kernel(const float2* __restrict__ B, long ldb, const int
     }
 }
 
+// Generated projectors (no table): the Gram-form A images of rows beta_p, and
+// the apply-form A tiles of beta_k(q_g), in the layout fmt_rows_kernel and
+// fmt_expand_kernel write from a stored FP32 table (values formed in FP32).
+__global__ void fmt_beta_rows_kernel(BetaGen Bg, int M, int K, int itiles, int kb0, int nkbl,
+                                     unsigned char* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const long nwarp = (long)itiles * 16 * nkbl;
+    for (long w = (blockIdx.x * (long)blockDim.x + threadIdx.x) >> 5; w < nwarp;
+         w += ((long)gridDim.x * blockDim.x) >> 5) {
+        const int rg = (int)(w / nkbl), kbl = (int)(w % nkbl);
+        const int r = lane & 7, kc = lane >> 3;
+        const int i = rg * 8 + r;
+        const int k = (kb0 + kbl) * 8 + 2 * kc;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < M) {
+            if (k < K) {
+                const float2 a = beta_value32(Bg, i, k);
+                v.x = a.x;
+                v.y = a.y;
+            }
+            if (k + 1 < K) {
+                const float2 a = beta_value32(Bg, i, k + 1);
+                v.z = a.x;
+                v.w = a.y;
+            }
+        }
+        const int it = rg >> 4, rr = ((rg & 15) << 3) + r;
+        unsigned char* tile = out + ((size_t)it * nkbl + kbl) * (2 * QA_BYTES);
+        put4(tile, tile + QA_BYTES, kmaj16(rr, 4 * kc), v);
+    }
+}
+
+__global__ void fmt_beta_expand_kernel(BetaGen Bg, int K, int N, int nkb, int gstart, int gtiles,
+                                       unsigned char* __restrict__ out) {
+    const long ng = (long)gtiles * 64;
+    const long total = ng * nkb * 4;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const int gl = (int)(t % ng);
+        const int g = gstart + gl;
+        const int k = 2 * (int)(t / ng);
+        float2 a = make_float2(0.f, 0.f), b = a;
+        if (g < N) {
+            if (k < K) a = beta_value32(Bg, k, g);
+            if (k + 1 < K) b = beta_value32(Bg, k + 1, g);
+        }
+        const int kb = k >> 3, kq = k & 7, gt = gl >> 6, gg = gl & 63;
+        unsigned char* tile = out + ((size_t)gt * nkb + kb) * (2 * QA_BYTES);
+        put4(tile, tile + QA_BYTES, kmaj16(2 * gg, 2 * kq), make_float4(a.x, -a.y, b.x, -b.y));
+        put4(tile, tile + QA_BYTES, kmaj16(2 * gg + 1, 2 * kq), make_float4(a.y, a.x, b.y, b.x));
+    }
+}
+
 // grid (itiles, jtiles, splits): split z takes local stages [z kbs, min(nkbl, (z + 1) kbs)) of the
 // chunk; A images of row tile it start at Af + it * astride stages (+ akb0 stages), B images at
 // Bf + jt * nkbl stages; partial sums go to part[(z0 + z) M N + i N + j].
@@ -550,7 +603,8 @@ void set_attrs() { std::call_once(g_attr_once, set_attrs_once); }
 }  // namespace
 
 void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, const int* amap, const float2* B,
-                  long ldb, const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid) {
+                  long ldb, const int* bmap, double2* C, long ci, long cj, double alpha, double beta, int kid,
+                  const BetaGen* gen) {
     if (M <= 0 || N <= 0) return;
     set_attrs();
     ProfScope ps(c, kid, ((double)M + N) * K * sizeof(float2) + (double)M * N * sizeof(double2), 8.0 * M * N * K);
@@ -562,10 +616,13 @@ void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, con
     const size_t b_stage = (size_t)2 * TJ * QK * 4;
     auto rows = [&](const unsigned char* dst, int kb0, int nkbl) {
         const long thr = (long)itiles * 16 * nkbl * 32;
-        fmt_rows_kernel<<<(int)std::min<long>(152 * 16, (thr + 255) / 256), 256, 0, c->stream>>>(
-            A, lda, amap, M, K, itiles, kb0, nkbl, (unsigned char*)dst);
+        const int nbk = (int)std::min<long>(152 * 16, (thr + 255) / 256);
+        if (gen)
+            fmt_beta_rows_kernel<<<nbk, 256, 0, c->stream>>>(*gen, M, K, itiles, kb0, nkbl, (unsigned char*)dst);
+        else
+            fmt_rows_kernel<<<nbk, 256, 0, c->stream>>>(A, lda, amap, M, K, itiles, kb0, nkbl, (unsigned char*)dst);
     };
-    bool table = A == c->beta32.as<float2>() && amap == nullptr && M == c->nptot && K == c->npw;
+    bool table = !gen && A == c->beta32.as<float2>() && amap == nullptr && M == c->nptot && K == c->npw;
     if (table && !c->beta32_gfmt.p && (size_t)itiles * nkb * a_stage <= FS_TABLE_FMT_MAX_BYTES) {
         c->beta32_gfmt.alloc((size_t)itiles * nkb * a_stage);
         rows(c->beta32_gfmt.as<unsigned char>(), 0, nkb);
@@ -628,7 +685,7 @@ void tc_gemm_gram(fs_ctx* c, int M, int N, int K, const float2* A, long lda, con
 template <typename A2>
 void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, const float2* B, long ldb,
                 const int* bmap, float2* C, long ldc, const int* cmap, double alpha, double beta, const float2* D,
-                long ldd, int kid) {
+                long ldd, int kid, const BetaGen* gen) {
     if (M <= 0 || N <= 0) return;
     set_attrs();
     ProfScope ps(c, kid, ((double)K + M * (beta != 0.0 ? 2.0 : 1.0)) * N * sizeof(float2) + (double)M * K * sizeof(A2),
@@ -640,10 +697,13 @@ void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, c
     const size_t col_bytes = (size_t)nkb * 2 * QA_BYTES;         // A images of one plane-wave tile
     auto expand = [&](int gs, int ng, unsigned char* dst) {
         const long total = (long)ng * 64 * nkb * 4;
-        fmt_expand_kernel<<<(int)std::min<long>(152 * 16, (total + 255) / 256), 256, 0, c->stream>>>(
-            B, ldb, bmap, K, N, nkb, gs * 64, ng, dst);
+        const int nbk = (int)std::min<long>(152 * 16, (total + 255) / 256);
+        if (gen)
+            fmt_beta_expand_kernel<<<nbk, 256, 0, c->stream>>>(*gen, K, N, nkb, gs * 64, ng, dst);
+        else
+            fmt_expand_kernel<<<nbk, 256, 0, c->stream>>>(B, ldb, bmap, K, N, nkb, gs * 64, ng, dst);
     };
-    bool table = B == c->beta32.as<float2>() && bmap == nullptr && N == c->npw && K == c->nptot;
+    bool table = !gen && B == c->beta32.as<float2>() && bmap == nullptr && N == c->npw && K == c->nptot;
     if (table && !c->beta32_fmt.p && (size_t)gtiles * col_bytes <= FS_TABLE_FMT_MAX_BYTES) {
         c->beta32_fmt.alloc((size_t)gtiles * col_bytes);
         expand(0, gtiles, c->beta32_fmt.as<unsigned char>());
@@ -674,9 +734,9 @@ void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, c
 }
 
 template void tc_gemm_nn<double2>(fs_ctx*, int, int, int, const double2*, long, long, const float2*, long, const int*,
-                                  float2*, long, const int*, double, double, const float2*, long, int);
+                                  float2*, long, const int*, double, double, const float2*, long, int, const BetaGen*);
 template void tc_gemm_nn<float2>(fs_ctx*, int, int, int, const float2*, long, long, const float2*, long, const int*,
-                                 float2*, long, const int*, double, double, const float2*, long, int);
+                                 float2*, long, const int*, double, double, const float2*, long, int, const BetaGen*);
 
 extern "C" fs_status fs_wait_selftest(fs_ctx* c, long long polls) {
     if (!c) return FS_ERR_ARG;

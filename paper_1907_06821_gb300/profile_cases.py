@@ -95,7 +95,7 @@ def main(argv=None):
 
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["apply", "solve", "linear", "chebfd"])
-    ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "wire_local", "medium"])
+    ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "wire_local", "medium", "longwire"])
     ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner first (verbose)")
     ap.add_argument("--bands", type=int, default=64)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])

@@ -123,8 +123,9 @@ def test_untrained_network_is_paper_preconditioner(fs, precision):
     assert np.array_equal(a["eps"], b["eps"])
 
 
-def test_trained_network_on_held_out_box(fs, capsys):
-    """Train on one seeded box, apply to a box of another seed (same sizes)."""
+def _held_out_iterations(fs):
+    """Train on one seeded box, apply to a box of another seed (same sizes); both
+    solves must reach the brute-force set.  Returns (loss, rows, {name: (iters, n_hpsi)})."""
     train = dense_box()
     test_box = fi.make_box(L=(16., 16., 24.), n=(24, 24, 36), ecut=4.0, natom=18, widths=(1.0,), nstates=40,
                            e_ref=None, seed=11)
@@ -146,11 +147,29 @@ def test_trained_network_on_held_out_box(fs, capsys):
             assert r["nconv"] == test_box.nstates
             assert np.abs(np.sort(r["eps"]) - np.sort(eb)).max() <= 1e-5
             iters[name] = (r["iters"], r["n_hpsi"])
+    return loss, rows, iters
+
+
+_HELD_OUT = {}
+
+
+def test_trained_network_keeps_the_solve_correct(fs, capsys):
+    """The trained network on a held-out box: the solve reaches the brute-force set
+    (the preconditioner changes the path, not the fixed point); the iteration counts
+    with and without it are reported."""
+    loss, rows, iters = _held_out_iterations(fs)
+    _HELD_OUT.update(iters)
     with capsys.disabled():
         print(f"\n[learned preconditioner] training loss {loss:.4f} on {rows} rows; held-out box: "
               f"M(G) {iters['M'][0]} iterations / {iters['M'][1]} H applications, "
               f"learned {iters['learned'][0]} / {iters['learned'][1]}")
-    # the network has not beaten M(G) on this machine (measured 95 to 115 iterations against 75,
-    # moving with rounding-level changes of its training data); the bound only guards against
-    # a learned gain that wrecks convergence
-    assert iters["learned"][1] <= 2.0 * iters["M"][1]
+
+
+@pytest.mark.xfail(reason="the trained network has not beaten the paper's M(G) on the held-out box: measured "
+                          "75 iterations / 7,344 H applications with M(G) against 90 to 115 / 8,840 to 11,216 "
+                          "with the network (the gain is the open question of this preconditioner)",
+                   strict=False)
+def test_trained_network_gains_over_paper_preconditioner(fs):
+    if not _HELD_OUT:
+        _HELD_OUT.update(_held_out_iterations(fs)[2])
+    assert _HELD_OUT["learned"][1] < _HELD_OUT["M"][1]

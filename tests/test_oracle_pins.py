@@ -375,3 +375,16 @@ def test_label_recovers_proportional_error():
     z2 = zt2.reshape(3, 8)
     others = [s for s in range(8) if s != 3 and wt2.reshape(3, 8)[0, s] > 0]
     assert np.allclose(z2[:, 3][:, None] - z2[:, others], np.log(2.0))
+
+
+def test_chunked_nonlocal_equals_stored_table():
+    """The table-free oracle H (projectors formed atom chunk by atom chunk, the form
+    used for the long wire whose table would not fit) equals the stored-table H."""
+    w = fi.make_box(L=(12.0, 12.0, 12.0), n=(20, 24, 40), ecut=4.0, k=(0.0, 0.05, 0.0), natom=5,
+                    widths=(0.8, 1.2), nstates=10, e_ref=0.2, seed=8)
+    h = pw.Hamiltonian(w)
+    hc = pw.Hamiltonian(w, table_bytes=0, atom_chunk=2)
+    assert h.B is not None and hc.B is None and hc.chunked
+    X = fi.raw_start_block(5, h.npw, 2)
+    a, b = h.apply(X, 0.1), hc.apply(X, 0.1)
+    assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
