@@ -774,8 +774,11 @@ fs_status solve_impl(fs_ctx* c, double e_ref, int nstates, double tol, fs_result
         S.init_block<double2>(B64);
         status = S.run<double2>(B64, std::max(0, c->opt.maxit - iters), tol, false, iters, 0, eps, resid, order, nres);
     }
-    if (status != 1) {
+    if (status != 1 && !done) {
         // not converged: report the current H-Ritz pairs of the wanted block
+        // (a passed FP64 check of a stalled FP32 stage has already filled them;
+        // the residual blocks exist only once FP64 iterations have run)
+        B64.alloc(m, npw);
         std::vector<double> ra, th;
         S.a_residuals(B64, ra, th);
         S.h_ritz<double2>(B64, th, nres, eps, resid, order);
