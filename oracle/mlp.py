@@ -19,14 +19,21 @@ network reproduces M(G) exactly).  Features of (band i, shell s):
     f2 = d_i / 0.1 Ha,  d_i = <x_i, (H-E) x_i>             (signed distance to E)
     f3 = log10(||R_i||) / 10
 
-Training label (per band and shell): the log of the gain that best maps the
-preconditioned residual onto the error e_i of the band,
+Training label (per band and shell): the per-shell gain that, for a
+preconditioner diagonal in the shells, would turn the preconditioned residual
+into the error e_i of the band -- the ratio of the error's magnitude to that
+of M R in the shell, both taken as shares of their band totals,
 
-    z*_{i,s} = log( max(Re<M R, e>_s / ||M R||_s^2, 1e-3) ) - (its weighted mean over s),
+    z*_{i,s} = clip( (1/2) log( (||e||_s^2 / ||e||^2) / (||M R||_s^2 / ||M R||^2) ),
+                     log 0.1, log 10 ),
 
 weighted by the shell's share of ||M R||^2; loss = weighted mean of
 (z - z*)^2.  Only the shell-relative part matters: the search direction is
-normalised before use.  Parameters are a flat float vector in the order
+normalised before use.  (A least-squares gain Re<M R, e>_s / ||M R||_s^2 was
+the first reading; its labels are dominated by the phase noise of e in the
+high shells, where it drives the gain to zero, and a network trained on them
+lost iterations on held-out boxes.  The magnitude ratio is the gain a diagonal
+operator with e = K R would have.)  Parameters are a flat float vector in the order
 W1[128][4], b1[128], W2[128][128], b2[128], W3[128][128], b3[128], W4[128], b4.
 """
 from __future__ import annotations
@@ -127,8 +134,8 @@ def features_and_labels(kin, ecut, nshell, M, R, E_err, d, shell):
     nb = R.shape[0]
     MR = M[None, :] * R
     F = np.zeros((nb, nshell, 4))
-    zt = np.zeros((nb, nshell))
-    wt = np.zeros((nb, nshell))
+    num = np.zeros((nb, nshell))
+    den = np.zeros((nb, nshell))
     centres = (np.arange(nshell) + 0.5) / nshell
     r2 = np.abs(R) ** 2
     mean_all = r2.mean(axis=1)
@@ -141,15 +148,15 @@ def features_and_labels(kin, ecut, nshell, M, R, E_err, d, shell):
         F[:, s, 1] = np.log10(np.maximum(ms, 1e-300) / np.maximum(mean_all, 1e-300))
         F[:, s, 2] = d / 0.1
         F[:, s, 3] = np.log10(np.maximum(np.linalg.norm(R, axis=1), 1e-300)) / 10.0
-        num = np.real(np.sum(np.conj(MR[:, sel]) * E_err[:, sel], axis=1))
-        den = np.sum(np.abs(MR[:, sel]) ** 2, axis=1)
-        g = np.where(den > 0, num / np.maximum(den, 1e-300), 0.0)
-        zt[:, s] = np.log(np.maximum(g, 1e-3))
-        wt[:, s] = den
-    tot = wt.sum(axis=1, keepdims=True)
-    wt = np.where(tot > 0, wt / np.maximum(tot, 1e-300), 0.0)
-    # relative to the band's weighted mean (a common factor does not change
-    # the normalised search direction)
-    zt = zt - np.sum(wt * zt, axis=1, keepdims=True)
+        num[:, s] = np.sum(np.abs(E_err[:, sel]) ** 2, axis=1)
+        den[:, s] = np.sum(np.abs(MR[:, sel]) ** 2, axis=1)
+    ntot = num.sum(axis=1, keepdims=True)
+    dtot = den.sum(axis=1, keepdims=True)
+    a = np.where(ntot > 0, num / np.maximum(ntot, 1e-300), 0.0)
+    wt = np.where(dtot > 0, den / np.maximum(dtot, 1e-300), 0.0)
+    lo, hi = np.log(0.1), np.log(10.0)
+    with np.errstate(divide="ignore"):
+        z = np.where(a > 0, 0.5 * np.log(np.maximum(a, 1e-300) / np.maximum(wt, 1e-300)), lo)
+    zt = np.where(wt > 0, np.clip(z, lo, hi), 0.0)
     F[:, :, 1] = np.maximum(F[:, :, 1], -30.0)
     return F.reshape(-1, 4), zt.ravel(), wt.ravel()

@@ -132,6 +132,13 @@ enum {
     KS_GRAM64,
     KS_ROTATE64,
     KS_VECTOR64,
+    // parts of the dense FP64 algebra, timed inside the scopes above (their
+    // times are contained in those of the enclosing classes, not added to them)
+    KS_SUB_POTRF,    // blocked Cholesky
+    KS_SUB_TRSM,     // blocked triangular solves
+    KS_SUB_HETRD,    // Householder reduction to tridiagonal form
+    KS_SUB_TRIEIG,   // tridiagonal eigenvalues (bisection) and vectors (inverse iteration)
+    KS_SUB_BACK,     // back-transformation of the eigenvectors (compact WY)
     KS_COUNT
 };
 // class of a step in the arithmetic of T2 (FP64 steps are counted apart)

@@ -45,13 +45,16 @@ __device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -
 // C[M x N] = alpha op(A) op(B) + beta C; opA/opB: 0 = N, 1 = C (conjugate transpose), opB 2 = T
 // Split K (gridDim.z > 1): block z takes k in [z kc, min(K, (z + 1) kc)) and
 // writes its partial product to C + z M N (ld M) with alpha = 1, beta = 0.
+// lower = 1: tiles wholly above the diagonal (every row index below every column
+// index) are skipped, for updates of which only the lower triangle is used.
 __global__ void __launch_bounds__(256) zgemm_kernel(int M, int N, int K, int opA, int opB, double alpha,
                                                     const double2* __restrict__ A, int lda,
                                                     const double2* __restrict__ B, int ldb, double beta,
-                                                    double2* __restrict__ C, int ldc, int kc) {
+                                                    double2* __restrict__ C, int ldc, int kc, int lower) {
     __shared__ double2 As[TK][TB + 1];
     __shared__ double2 Bs[TK][TB + 1];
     const int m0 = blockIdx.x * TB, n0 = blockIdx.y * TB;
+    if (lower && m0 + TB <= n0) return;
     if (gridDim.z > 1) {
         const int k0 = blockIdx.z * kc;
         K = min(K - k0, kc);
@@ -551,28 +554,41 @@ __global__ void tri_bisect_kernel(const double* d, const double* e2, int n, int 
 }
 
 // ------------------------------------------------------------------ tridiagonal eigenvectors
-// Inverse iteration for the clusters of w (ascending), one warp per index: the
-// warp of index k0 starts a cluster when w[k0] - w[k0 - 1] > 1e-10 ||T|| and
-// computes the cluster's vectors in order, each made orthogonal to the
-// cluster's earlier ones.  An eigenvector from inverse iteration is accurate
-// to about eps ||T|| / gap, so vectors outside a cluster are orthogonal to
-// 1e-6 or better; eigenvalues closer than that (the E +- d pairs of the folded
-// spectrum, an orthonormal block's unit eigenvalues) share a cluster.  Lane 0
-// runs the elimination and the substitutions (sequential in the position),
-// all lanes the Gram-Schmidt steps and the norms.  z: [n][m] real
-// (position-major), work: [n][5][m] elimination factors.
-__global__ void tri_invit_kernel(const double* d, const double* e, int n, int m, const double* w,
-                                 const double* info3, double* z, double* work) {
-    const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+// Inverse iteration for the clusters of w (ascending), one warp (block) per
+// index: the block of index k0 starts a cluster when w[k0] - w[k0 - 1] >
+// 1e-10 ||T|| and computes the cluster's vectors in order, each made
+// orthogonal to the cluster's earlier ones.  An eigenvector from inverse
+// iteration is accurate to about eps ||T|| / gap, so vectors outside a cluster
+// are orthogonal to 1e-6 or better; eigenvalues closer than that (the E +- d
+// pairs of the folded spectrum, an orthonormal block's unit eigenvalues) share
+// a cluster.  Lane 0 runs the elimination and the substitutions (sequential in
+// the position) on shared-memory copies of T, of the factors and of the
+// vector; all lanes run the Gram-Schmidt steps and the norms.  z: [n][m] real
+// (position-major).  Dynamic shared memory: 8 n doubles.
+__global__ void __launch_bounds__(32) tri_invit_kernel(const double* d, const double* e, int n, int m,
+                                                       const double* w, const double* info3, double* z) {
+    extern __shared__ __align__(16) double tsm[];
+    double* dd = tsm;          // diagonal of T
+    double* ee = dd + n;       // off-diagonal of T (ee[n - 1] = 0)
+    double* ri = ee + n;       // pivot of row i of U
+    double* u1 = ri + n;       // first and second super-diagonals of U
+    double* u2 = u1 + n;
+    double* mu = u2 + n;       // multipliers
+    double* sw = mu + n;       // 1 where rows i and i + 1 were swapped
+    double* zv = sw + n;       // the vector being iterated
+    const int k0 = blockIdx.x;
+    const int lane = threadIdx.x;
     if (k0 >= m) return;
     const double tnorm = fmax(info3[3], 1e-300);
     const double ctol = 1e-10 * tnorm;
-    if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;  // not a cluster start (warp-uniform)
+    if (k0 > 0 && w[k0] - w[k0 - 1] <= ctol) return;  // not a cluster start (block-uniform)
     int k1 = k0 + 1;
     while (k1 < m && w[k1] - w[k1 - 1] <= ctol) ++k1;
-    // factor f of position i for this cluster: work[(i * 5 + f) * m + k0]
-#define WK(f, i) work[((long)(i) * 5 + (f)) * m + k0]
+    for (int i = lane; i < n; i += 32) {
+        dd[i] = d[i];
+        ee[i] = i < n - 1 ? e[i] : 0.0;
+    }
+    __syncwarp();
 #define ZV(q, i) z[(long)(i) * m + (q)]
     const double sep = 10.0 * DBL_EPSILON * tnorm;
     double lam_prev = -1e300;
@@ -581,59 +597,59 @@ __global__ void tri_invit_kernel(const double* d, const double* e, int n, int m,
         if (lam - lam_prev < sep) lam = lam_prev + sep;  // separate equal eigenvalues of a cluster
         lam_prev = lam;
         if (lane == 0) {
-            // elimination with partial pivoting of T - lam I: U rows (u0, u1, u2), multipliers, swaps
-            double p0 = d[0] - lam, p1 = n > 1 ? e[0] : 0.0, p2 = 0.0;
+            // elimination with partial pivoting of T - lam I: U rows (pivot, u1, u2), multipliers, swaps
+            double p0 = dd[0] - lam, p1 = n > 1 ? ee[0] : 0.0, p2 = 0.0;
             for (int i = 0; i < n - 1; ++i) {
-                const double s = e[i], a = d[i + 1] - lam, t = i + 1 < n - 1 ? e[i + 1] : 0.0;
-                if (fabs(p0) >= fabs(s)) {
+                const double sv = ee[i], a = dd[i + 1] - lam, t = ee[i + 1];
+                if (fabs(p0) >= fabs(sv)) {
                     if (p0 == 0.0) p0 = sep;
-                    const double mu = s / p0;
-                    WK(0, i) = p0; WK(1, i) = p1; WK(2, i) = p2; WK(3, i) = mu; WK(4, i) = 0.0;
-                    p0 = a - mu * p1;
-                    p1 = t - mu * p2;
+                    const double f = sv / p0;
+                    ri[i] = p0; u1[i] = p1; u2[i] = p2; mu[i] = f; sw[i] = 0.0;
+                    p0 = a - f * p1;
+                    p1 = t - f * p2;
                     p2 = 0.0;
                 } else {
-                    const double mu = p0 / s;
-                    WK(0, i) = s; WK(1, i) = a; WK(2, i) = t; WK(3, i) = mu; WK(4, i) = 1.0;
-                    p0 = p1 - mu * a;
-                    p1 = p2 - mu * t;
+                    const double f = p0 / sv;
+                    ri[i] = sv; u1[i] = a; u2[i] = t; mu[i] = f; sw[i] = 1.0;
+                    p0 = p1 - f * a;
+                    p1 = p2 - f * t;
                     p2 = 0.0;
                 }
             }
-            WK(0, n - 1) = p0 == 0.0 ? sep : p0;
+            ri[n - 1] = p0 == 0.0 ? sep : p0;
             for (int i = 0; i < n - 1; ++i) {
-                const double u = WK(0, i);
-                if (fabs(u) < sep) WK(0, i) = u < 0 ? -sep : sep;
+                const double u = ri[i];
+                if (fabs(u) < sep) ri[i] = u < 0 ? -sep : sep;
             }
             // start vector: a fixed pseudo-random sequence per index
             unsigned int st = 2654435761u * (unsigned int)(k + 1) + 12345u;
             for (int i = 0; i < n; ++i) {
                 st = st * 1664525u + 1013904223u;
-                ZV(k, i) = 0.5 + (double)(st >> 8) * (1.0 / 16777216.0);
+                zv[i] = 0.5 + (double)(st >> 8) * (1.0 / 16777216.0);
             }
         }
         __syncwarp();
         for (int it = 0; it < 4; ++it) {
             if (lane == 0) {
                 // forward: apply the row operations
-                double xi = ZV(k, 0);
+                double xi = zv[0];
                 for (int i = 0; i < n - 1; ++i) {
-                    const double xn = ZV(k, i + 1);
-                    if (WK(4, i) != 0.0) {
-                        ZV(k, i) = xn;
-                        xi = xi - WK(3, i) * xn;
+                    const double xn = zv[i + 1];
+                    if (sw[i] != 0.0) {
+                        zv[i] = xn;
+                        xi = xi - mu[i] * xn;
                     } else {
-                        ZV(k, i) = xi;
-                        xi = xn - WK(3, i) * xi;
+                        zv[i] = xi;
+                        xi = xn - mu[i] * xi;
                     }
                 }
-                ZV(k, n - 1) = xi;
+                zv[n - 1] = xi;
                 // back substitution with the three diagonals of U
-                double x2 = 0.0, x1 = ZV(k, n - 1) / WK(0, n - 1);
-                ZV(k, n - 1) = x1;
+                double x2 = 0.0, x1 = zv[n - 1] / ri[n - 1];
+                zv[n - 1] = x1;
                 for (int i = n - 2; i >= 0; --i) {
-                    const double x0 = (ZV(k, i) - WK(1, i) * x1 - WK(2, i) * x2) / WK(0, i);
-                    ZV(k, i) = x0;
+                    const double x0 = (zv[i] - u1[i] * x1 - u2[i] * x2) / ri[i];
+                    zv[i] = x0;
                     x2 = x1;
                     x1 = x0;
                 }
@@ -642,20 +658,21 @@ __global__ void tri_invit_kernel(const double* d, const double* e, int n, int m,
             // orthogonalise against the cluster's earlier vectors (warp-parallel), normalise
             for (int q = k0; q < k; ++q) {
                 double dot = 0;
-                for (int i = lane; i < n; i += 32) dot += ZV(q, i) * ZV(k, i);
+                for (int i = lane; i < n; i += 32) dot += ZV(q, i) * zv[i];
                 for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-                for (int i = lane; i < n; i += 32) ZV(k, i) -= dot * ZV(q, i);
+                for (int i = lane; i < n; i += 32) zv[i] -= dot * ZV(q, i);
                 __syncwarp();
             }
             double nrm = 0;
-            for (int i = lane; i < n; i += 32) nrm += ZV(k, i) * ZV(k, i);
+            for (int i = lane; i < n; i += 32) nrm += zv[i] * zv[i];
             for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
             const double inv = nrm > 0 ? 1.0 / sqrt(nrm) : 1.0;
-            for (int i = lane; i < n; i += 32) ZV(k, i) *= inv;
+            for (int i = lane; i < n; i += 32) zv[i] *= inv;
             __syncwarp();
         }
+        for (int i = lane; i < n; i += 32) ZV(k, i) = zv[i];
+        __syncwarp();
     }
-#undef WK
 #undef ZV
 }
 
@@ -721,10 +738,11 @@ inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
 // C = alpha sum_z P[z] + beta C, z in order
 __global__ void gemm_sum_kernel(int M, int N, int splits, const double2* P, double alpha, double beta, double2* C,
-                                int ldc) {
+                                int ldc, int lower) {
     long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (t >= (long)M * N) return;
     const int r = (int)(t % M), col = (int)(t / M);
+    if (lower && (r / TB + 1) * TB <= (col / TB) * TB) return;  // a tile the GEMM skipped
     double2 s = P[t];
     for (int z = 1; z < splits; ++z) s = cadd(s, P[(size_t)z * M * N + t]);
     double2* c = C + r + (long)col * ldc;
@@ -742,8 +760,9 @@ __global__ void gemm_sum_kernel(int M, int N, int splits, const double2* P, doub
 // C = alpha op(A) op(B) + beta C; when the output has few tiles and K is long,
 // K is split over the grid's z dimension into partial products that a second
 // kernel adds in a fixed order (deterministic).
-void dense_gemm(fs_ctx* c, int opA, int opB, int M, int N, int K, double alpha, const double2* A, int lda,
-                const double2* B, int ldb, double beta, double2* C, int ldc) {
+namespace {
+void dense_gemm_impl(fs_ctx* c, int opA, int opB, int M, int N, int K, double alpha, const double2* A, int lda,
+                     const double2* B, int ldb, double beta, double2* C, int ldc, int lower) {
     if (M <= 0 || N <= 0) return;
     K = std::max(K, 0);
     const int tiles = cdiv(M, TB) * cdiv(N, TB);
@@ -751,7 +770,7 @@ void dense_gemm(fs_ctx* c, int opA, int opB, int M, int N, int K, double alpha, 
     if (tiles < 152 && K >= 8 * TK) splits = std::min(std::max(1, 304 / tiles), std::max(1, K / (4 * TK)));
     if (splits <= 1) {
         dim3 g(cdiv(M, TB), cdiv(N, TB));
-        zgemm_kernel<<<g, 256, 0, c->stream>>>(M, N, K, opA, opB, alpha, A, lda, B, ldb, beta, C, ldc, K);
+        zgemm_kernel<<<g, 256, 0, c->stream>>>(M, N, K, opA, opB, alpha, A, lda, B, ldb, beta, C, ldc, K, lower);
         FS_CUDA(cudaGetLastError());
         return;
     }
@@ -761,15 +780,22 @@ void dense_gemm(fs_ctx* c, int opA, int opB, int M, int N, int K, double alpha, 
     D.gpart.ensure((size_t)splits * M * N * sizeof(double2));
     double2* P = D.gpart.as<double2>();
     dim3 g(cdiv(M, TB), cdiv(N, TB), splits);
-    zgemm_kernel<<<g, 256, 0, c->stream>>>(M, N, K, opA, opB, 1.0, A, lda, B, ldb, 0.0, P, M, kc);
-    gemm_sum_kernel<<<cdiv((long)M * N, 256), 256, 0, c->stream>>>(M, N, splits, P, alpha, beta, C, ldc);
+    zgemm_kernel<<<g, 256, 0, c->stream>>>(M, N, K, opA, opB, 1.0, A, lda, B, ldb, 0.0, P, M, kc, lower);
+    gemm_sum_kernel<<<cdiv((long)M * N, 256), 256, 0, c->stream>>>(M, N, splits, P, alpha, beta, C, ldc, lower);
     FS_CUDA(cudaGetLastError());
+}
+}  // namespace
+
+void dense_gemm(fs_ctx* c, int opA, int opB, int M, int N, int K, double alpha, const double2* A, int lda,
+                const double2* B, int ldb, double beta, double2* C, int ldc) {
+    dense_gemm_impl(c, opA, opB, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, 0);
 }
 
 // Cholesky of the lower triangle of A (n x n, ld lda); squared pivots to piv
 // (device, may be null).  Returns the LAPACK info (0, or the first failing
 // column + 1).  Synchronises the context's stream.
 int dense_potrf(fs_ctx* c, int n, double2* A, int lda, double* piv) {
+    ProfScope ps(c, KS_SUB_POTRF, 0.0, 8.0 * n * (double)n * n / 3.0);
     DenseWork& D = c->dense;
     D.info.ensure(sizeof(int));
     int* info = D.info.as<int>();
@@ -780,8 +806,9 @@ int dense_potrf(fs_ctx* c, int n, double2* A, int lda, double* piv) {
         const int rest = n - j0 - b;
         if (rest > 0) {
             potrf_panel_kernel<<<cdiv((long)rest * 32, 256), 256, 0, c->stream>>>(A, lda, n, j0, b);
-            dense_gemm(c, 0, 1, rest, rest, b, -1.0, A + j0 + b + (long)j0 * lda, lda, A + j0 + b + (long)j0 * lda,
-                       lda, 1.0, A + j0 + b + (long)(j0 + b) * lda, lda);
+            // trailing update of the lower triangle (the upper one is never read)
+            dense_gemm_impl(c, 0, 1, rest, rest, b, -1.0, A + j0 + b + (long)j0 * lda, lda,
+                            A + j0 + b + (long)j0 * lda, lda, 1.0, A + j0 + b + (long)(j0 + b) * lda, lda, 1);
         }
     }
     FS_CUDA(cudaGetLastError());
@@ -794,6 +821,7 @@ int dense_potrf(fs_ctx* c, int n, double2* A, int lda, double* piv) {
 // B <- L^-1 B (conj = 0) or L^-H B (conj = 1); L lower n x n (ld lda), B n x ncols (ld ldb)
 void dense_trsm(fs_ctx* c, int conj, int n, int ncols, const double2* L, int lda, double2* B, int ldb) {
     if (n <= 0 || ncols <= 0) return;
+    ProfScope ps(c, KS_SUB_TRSM, 0.0, 4.0 * n * (double)n * ncols);
     const int nblk = cdiv(n, NBLK);
     for (int q = 0; q < nblk; ++q) {
         const int bi = conj ? nblk - 1 - q : q;
@@ -830,7 +858,6 @@ void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int 
     D.e2.ensure((size_t)n * sizeof(double));
     D.Y.ensure((size_t)((n + SEG - 1) / SEG) * n * sizeof(double2));
     D.z.ensure((size_t)n * m * sizeof(double));
-    D.work.ensure((size_t)5 * n * m * sizeof(double));
     D.info3.ensure(4 * sizeof(double));
     D.bar.ensure(2 * sizeof(unsigned int));
     int dev = 0, nsm = 0;
@@ -840,12 +867,16 @@ void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int 
     if (!D.attr_set) {
         FS_CUDA(cudaFuncSetAttribute((const void*)hetrd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      3 * FS_DENSE_MAX_N * (int)sizeof(double2)));
+        FS_CUDA(cudaFuncSetAttribute((const void*)tri_invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     8 * FS_DENSE_MAX_N * (int)sizeof(double)));
         D.attr_set = true;
     }
     int per_sm = 0;
     FS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hetrd_kernel, 256, smem));
     // enough warps for the (column, segment) units, at most one block per SM
     const int nblocks = std::max(1, std::min({nsm, nsm * std::max(per_sm, 1), (n + 3) / 4}));
+    {
+    ProfScope ps_h(c, KS_SUB_HETRD, 0.0, 16.0 * n * (double)n * n / 3.0);
     hermitize_kernel<<<cdiv((long)n * n, 256), 256, 0, c->stream>>>(A, n);
     FS_CUDA(cudaMemsetAsync(D.bar.p, 0, 2 * sizeof(unsigned int), c->stream));
     FS_CUDA(cudaMemsetAsync(D.V.p, 0, (size_t)n * n * sizeof(double2), c->stream));
@@ -866,15 +897,20 @@ void dense_heev(fs_ctx* c, int n, double2* A, int m, double* w, double2* Z, int 
         // no reflector: T = A
         FS_CUDA(cudaMemsetAsync(D.tau.p, 0, sizeof(double2), c->stream));
     }
+    }
+    {
+    ProfScope ps_t(c, KS_SUB_TRIEIG, 0.0, 0.0);
     tri_prep_kernel<<<1, 256, 0, c->stream>>>(D.d.as<double>(), D.e.as<double>(), D.e2.as<double>(), n,
                                               D.info3.as<double>());
     tri_bisect_kernel<<<m, 32, 0, c->stream>>>(D.d.as<double>(), D.e2.as<double>(), n, m,
                                                                       D.info3.as<double>(), w);
-    tri_invit_kernel<<<cdiv((long)m * 32, 128), 128, 0, c->stream>>>(D.d.as<double>(), D.e.as<double>(), n, m, w,
-                                                        D.info3.as<double>(), D.z.as<double>(), D.work.as<double>());
+    tri_invit_kernel<<<m, 32, (size_t)8 * n * sizeof(double), c->stream>>>(D.d.as<double>(), D.e.as<double>(), n, m,
+                                                                           w, D.info3.as<double>(), D.z.as<double>());
     tri_z_to_Z_kernel<<<cdiv((long)n * m, 256), 256, 0, c->stream>>>(n, m, D.z.as<double>(), Z, ldz);
     FS_CUDA(cudaGetLastError());
+    }
     if (n > 1) {
+        ProfScope ps_b(c, KS_SUB_BACK, 0.0, 8.0 * n * (double)n * m);
         const int nref = n - 1, nblkr = cdiv(nref, NBLK);
         D.wyT.ensure((size_t)nblkr * NBLK * NBLK * sizeof(double2));
         D.wyW.ensure((size_t)NBLK * m * sizeof(double2));

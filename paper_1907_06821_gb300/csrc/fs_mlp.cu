@@ -234,8 +234,8 @@ __global__ void adam_kernel(float* P, const float* __restrict__ g, float* m, flo
     P[p] -= lr * (mm / bc1) / (sqrtf(vv / bc2) + 1e-8f);
 }
 
-// per (band a, shell s): sum over the shell of |R|^2 (and, with E, of
-// Re<M R, E> and |M R|^2); shells are contiguous ranges of a permutation
+// per (band a, shell s): sum over the shell of |R|^2 (and, with E, of |E|^2
+// and |M R|^2); shells are contiguous ranges of a permutation
 template <typename T2>
 __global__ void shell_stats_kernel(const T2* __restrict__ R, const int* __restrict__ act, const T2* __restrict__ Err,
                                    long npw, const int* __restrict__ perm, const int* __restrict__ off,
@@ -255,7 +255,7 @@ __global__ void shell_stats_kernel(const T2* __restrict__ R, const int* __restri
         if (e) {
             double mm = M[gidx];
             T2 q = e[gidx];
-            s1 += mm * ((double)v.x * q.x + (double)v.y * q.y);
+            s1 += (double)q.x * q.x + (double)q.y * q.y;
             s2 += mm * mm * p;
         }
     }
@@ -277,6 +277,9 @@ __global__ void shell_stats_kernel(const T2* __restrict__ R, const int* __restri
     }
 }
 
+constexpr double LABEL_LO = -2.302585092994046;  // log 0.1
+constexpr double LABEL_HI = 2.302585092994046;   // log 10
+
 // features of (band a, shell s) from the shell sums; labels/weights when num != null
 __global__ void features_kernel(const double* __restrict__ r2, const double* __restrict__ num,
                                 const double* __restrict__ den, const double2* __restrict__ dots,
@@ -284,15 +287,17 @@ __global__ void features_kernel(const double* __restrict__ r2, const double* __r
                                 long npw, float* __restrict__ F, float* __restrict__ zt, float* __restrict__ wt) {
     int a = blockIdx.x;
     if (a >= na) return;
-    __shared__ double tot, dtot;
+    __shared__ double tot, dtot, ntot;
     if (threadIdx.x == 0) {
-        double t = 0, dt = 0;
+        double t = 0, dt = 0, nt = 0;
         for (int s = 0; s < nshell; ++s) {
             t += r2[(long)a * nshell + s];
             if (den) dt += den[(long)a * nshell + s];
+            if (num) nt += num[(long)a * nshell + s];
         }
         tot = t;
         dtot = dt;
+        ntot = nt;
     }
     __syncthreads();
     const int band = act ? act[a] : a;
@@ -307,22 +312,16 @@ __global__ void features_kernel(const double* __restrict__ r2, const double* __r
         F[row * 4 + 2] = (float)(d / 0.1);
         F[row * 4 + 3] = (float)(log10(fmax(sqrt(tot), 1e-300)) / 10.0);
         if (num) {
-            double g = den[row] > 0 ? num[row] / den[row] : 0.0;
-            zt[row] = (float)log(fmax(g, 1e-3));
-            wt[row] = (float)(dtot > 0 ? den[row] / dtot : 0.0);
+            // log of the shell's share of the error over its share of the
+            // preconditioned residual, halved (a ratio of magnitudes), clipped
+            // to [log 0.1, log 10]; weight: the shell's share of |M R|^2
+            const double b = dtot > 0 ? den[row] / dtot : 0.0;
+            const double an = ntot > 0 ? num[row] / ntot : 0.0;
+            double z = 0.0;
+            if (b > 0) z = an > 0 ? 0.5 * log(an / b) : LABEL_LO;
+            zt[row] = (float)fmin(fmax(z, LABEL_LO), LABEL_HI);
+            wt[row] = (float)b;
         }
-    }
-    // labels relative to the band's weighted mean: a common factor on all the
-    // shells of a band does not change the search direction (it is normalised)
-    if (num) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double mu = 0;
-            for (int s = 0; s < nshell; ++s) mu += (double)wt[(long)a * nshell + s] * zt[(long)a * nshell + s];
-            tot = mu;
-        }
-        __syncthreads();
-        for (int s = threadIdx.x; s < nshell; s += blockDim.x) zt[(long)a * nshell + s] -= (float)tot;
     }
 }
 

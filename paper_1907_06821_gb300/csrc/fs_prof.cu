@@ -9,7 +9,9 @@ const char* const KS_NAMES[KS_COUNT] = {"col_inverse_fft", "plane_fft_vloc", "co
                                         "gram",            "rotate",         "vector",
                                         "dense_la",        "col_inverse_fft_fp64", "plane_fft_vloc_fp64",
                                         "col_forward_fft_fp64", "nonlocal_project_fp64", "nonlocal_add_fp64",
-                                        "gram_fp64",       "rotate_fp64",    "vector_fp64"};
+                                        "gram_fp64",       "rotate_fp64",    "vector_fp64",
+                                        "dense.potrf",     "dense.trsm",     "dense.hetrd",
+                                        "dense.tridiag_eig", "dense.backtransform"};
 
 cudaEvent_t take(fs_ctx* c) {
     if (!c->prof.pool.empty()) {
@@ -36,11 +38,12 @@ ProfScope::ProfScope(fs_ctx* c_, int id_, double bytes, double flops) : c(c_), i
 ProfScope::~ProfScope() {
     if (!a) return;
     cudaEvent_t b = nullptr;
-    if (cudaEventCreate(&b) != cudaSuccess) return;
     if (!c->prof.pool.empty()) {
-        cudaEventDestroy(b);
         b = c->prof.pool.back();
         c->prof.pool.pop_back();
+    } else if (cudaEventCreate(&b) != cudaSuccess) {
+        c->prof.pool.push_back(a);
+        return;
     }
     cudaEventRecord(b, c->stream);
     c->prof.pend.push_back({id, a, b});

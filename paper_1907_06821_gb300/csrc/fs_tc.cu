@@ -166,6 +166,10 @@ constexpr int QSTAGE = 2 * QA_BYTES + 2 * QB_MAX;
 constexpr int QDRAIN = 16;                    // stages per tensor-memory chain
 constexpr int QTHREADS = 320;
 constexpr int QSMEM = QS * QSTAGE + 128;
+// persistent apply form: as many stages of the actual tile size as fit
+constexpr int QS_MAX = 8;
+constexpr int QSMEM_MAX = 232448;             // the opt-in shared memory of one block
+constexpr int QCTL_BYTES = 256;               // barriers and the tensor-memory slot
 
 __host__ __device__ __forceinline__ uint32_t kmaj16(int row, int k) {
     return (uint32_t)((((row >> 3) * (QK / 4) + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2));
@@ -260,15 +264,16 @@ struct QCtl {
     uint32_t tmem;
 };
 
-__device__ __forceinline__ QCtl tcq_setup(unsigned char* smem) {
+// nst stages of sbytes each, then the barriers (nst <= QS_MAX)
+__device__ __forceinline__ QCtl tcq_setup(unsigned char* smem, int nst = QS, uint32_t sbytes = QSTAGE) {
     QCtl t;
-    t.full = reinterpret_cast<uint64_t*>(smem + QS * QSTAGE);
-    t.empty = t.full + QS;
-    t.accf = t.empty + QS;
+    t.full = reinterpret_cast<uint64_t*>(smem + (size_t)nst * sbytes);
+    t.empty = t.full + nst;
+    t.accf = t.empty + nst;
     t.acce = t.accf + 2;
     uint32_t* tslot = reinterpret_cast<uint32_t*>(t.acce + 2);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < QS; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init_n(&t.full[s], 1);
             mbar_init_n(&t.empty[s], 1);
         }
@@ -391,37 +396,137 @@ __device__ __forceinline__ bool tcq_pipeline(const QCtl& t, unsigned char* smem,
     return ok;
 }
 
+// Persistent apply form: each block walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (t -> coefficient tile it = t mod itiles,
+// plane-wave tile gt = t / itiles, so the blocks that share a plane-wave tile
+// run side by side and its images come from L2 the second time).  The copy
+// and MMA threads run ahead across tile boundaries with global stage and
+// chain counters, so one tile's epilogue overlaps the next tile's copies and
+// MMAs; the ring holds nst stages of the tile's actual size.
 __global__ void __launch_bounds__(QTHREADS, 1)
-tcq_nn_kernel(int M, int N, int nkb, int TI, int gt0, const unsigned char* __restrict__ Af,
-              const unsigned char* __restrict__ Bf, float2* C, long ldc, const int* __restrict__ cmap, float alpha,
-              float beta, const float2* D, long ldd, int* errflag) {
+tcq_nn_kernel(int M, int N, int nkb, int TI, int itiles, int ntiles, int gt0, int nst,
+              const unsigned char* __restrict__ Af, const unsigned char* __restrict__ Bf, float2* C, long ldc,
+              const int* __restrict__ cmap, float alpha, float beta, const float2* D, long ldd, int* errflag) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const QCtl t = tcq_setup(smem);
+    const uint32_t bsplit = (uint32_t)TI * QK * 4;
+    const uint32_t sbytes = 2 * QA_BYTES + 2 * bsplit;
+    const QCtl t = tcq_setup(smem, nst, sbytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int it = blockIdx.x, gt = blockIdx.y;
-    const int i0 = it * TI, ni = min(TI, M - i0), g0 = (gt0 + gt) * 64;
-    Acc acc;
-    const bool ok = tcq_pipeline(t, smem, Af + (size_t)gt * nkb * (2 * QA_BYTES),
-                                 Bf + (size_t)it * nkb * (2 * (size_t)TI * QK * 4), nkb, TI, acc);
-    if (ok && warp >= 2) {
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {
+            long long g = 0;  // stages issued by this block
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int it = tile % itiles, gt = tile / itiles;
+                const unsigned char* a = Af + (size_t)gt * nkb * (2 * QA_BYTES);
+                const unsigned char* b = Bf + (size_t)it * nkb * (2 * (size_t)bsplit);
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int st = (int)(g % nst);
+                    if (g >= nst && !mbar_wait(&t.empty[st], (uint32_t)((g / nst) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* dst = smem + (size_t)st * sbytes;
+                    mbar_expect_tx(&t.full[st], sbytes);
+                    bulk_g2s(dst, a + (size_t)kb * (2 * QA_BYTES), 2 * QA_BYTES, &t.full[st]);
+                    bulk_g2s(dst + 2 * QA_BYTES, b + (size_t)kb * (2 * bsplit), 2 * bsplit, &t.full[st]);
+                }
+            }
+            // every copy issued has landed before the block can exit
+            for (long long q = g > nst ? g - nst : 0; q < g; ++q)
+                if (!mbar_wait(&t.full[q % nst], (uint32_t)(q / nst) & 1)) ok = false;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(TM, TI);
+            long long g = 0, last = -1;
+            int ch = 0;  // accumulator chains started by this block
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int st = (int)(g % nst), buf = ch & 1;
+                    const bool first = kb % QDRAIN == 0;
+                    if (!mbar_wait(&t.full[st], (uint32_t)(g / nst) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (first && ch >= 2 && !mbar_wait(&t.acce[buf], ((ch >> 1) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = smem_u32(smem + (size_t)st * sbytes);
+                    const uint32_t ahi = base, alo = base + QA_BYTES, bhi = base + 2 * QA_BYTES, blo = bhi + bsplit;
+                    const uint32_t d = t.tmem + (uint32_t)(buf * 256);
+#pragma unroll
+                    for (int ks = 0; ks < QK / 8; ++ks) {
+                        const uint32_t o = ks * 256;
+                        mma_tf32(d, sdesc16(ahi + o), sdesc16(bhi + o), idesc, (first && ks == 0) ? 0u : 1u);
+                        mma_tf32(d, sdesc16(ahi + o), sdesc16(blo + o), idesc, 1u);
+                        mma_tf32(d, sdesc16(alo + o), sdesc16(bhi + o), idesc, 1u);
+                    }
+                    mma_commit(&t.empty[st]);
+                    if (kb % QDRAIN == QDRAIN - 1 || kb == nkb - 1) {
+                        mma_commit(&t.accf[buf]);
+                        ++ch;
+                    }
+                    last = g;
+                }
+            }
+            // the MMAs issued have completed before tensor memory is released
+            if (last >= 0 && !mbar_wait(&t.empty[last % nst], (uint32_t)(last / nst) & 1)) ok = false;
+        }
+    } else {
         const int q = warp & 3, h = (warp - 2) >> 2;
+        const int nchain = (nkb + QDRAIN - 1) / QDRAIN;
         const int r = 32 * q + lane;  // j' = 2 g + c
-        const int g = g0 + (r >> 1);
         const int comp = r & 1;
         float* Cf = reinterpret_cast<float*>(C);
         const float* Df = reinterpret_cast<const float*>(D);
-        if (g < N) {
+        int ch = 0;
+        Acc acc;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int it = tile % itiles, gt = tile / itiles;
+            const int i0 = it * TI, ni = min(TI, M - i0), g = (gt0 + gt) * 64 + (r >> 1);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c0 = 128 * h + 32 * j;
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const int ii = c0 + e;
-                    if (ii < ni) {
-                        const long row = cmap ? (long)cmap[i0 + ii] : (long)(i0 + ii);
-                        float o = alpha * acc.v[j][e];
-                        if (beta != 0.f) o += beta * Df[(row * ldd + g) * 2 + comp];
-                        Cf[(row * ldc + g) * 2 + comp] = o;
+                for (int e = 0; e < 32; ++e) acc.v[j][e] = 0.f;
+            for (int cc = 0; cc < nchain; ++cc, ++ch) {
+                const int buf = ch & 1;
+                // every lane polls; the vote keeps the warp together if one gives up
+                if (!__all_sync(0xffffffffu, mbar_wait(&t.accf[buf], (ch >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c0 = 128 * h + 32 * j;
+                    if (c0 < TI) {  // warp-uniform
+                        float v[32];
+                        tmem_ld32(t.tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * 256 + c0), v);
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) acc.v[j][e] += v[e];
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&t.acce[buf]);
+            }
+            if (!ok) break;
+            if (g < N) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c0 = 128 * h + 32 * j;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const int ii = c0 + e;
+                        if (ii < ni) {
+                            const long row = cmap ? (long)cmap[i0 + ii] : (long)(i0 + ii);
+                            float o = alpha * acc.v[j][e];
+                            if (beta != 0.f) o += beta * Df[(row * ldd + g) * 2 + comp];
+                            Cf[(row * ldc + g) * 2 + comp] = o;
+                        }
                     }
                 }
             }
@@ -595,7 +700,7 @@ __global__ void wait_selftest_kernel(long long limit, int* errflag) {
 
 std::once_flag g_attr_once;
 void set_attrs_once() {
-    cudaFuncSetAttribute((const void*)tcq_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QSMEM);
+    cudaFuncSetAttribute((const void*)tcq_nn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QSMEM_MAX);
     cudaFuncSetAttribute((const void*)tcq_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, QSMEM);
 }
 void set_attrs() { std::call_once(g_attr_once, set_attrs_once); }
@@ -716,6 +821,15 @@ void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, c
             A, ai, ak, M, K, TI, itiles, nkb, c->bfmt.as<unsigned char>());
     }
     const int chunk = table ? gtiles : (int)std::max<size_t>(1, std::min<size_t>(gtiles, FS_FMT_CHUNK_BYTES / col_bytes));
+    // ring of the persistent kernel: as many stages of this tile size as fit
+    const size_t sbytes = (size_t)2 * QA_BYTES + (size_t)2 * TI * QK * 4;
+    const int nst = (int)std::min<size_t>(QS_MAX, (QSMEM_MAX - QCTL_BYTES) / sbytes);
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0;
+        FS_CUDA(cudaGetDevice(&dev));
+        FS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
     for (int gs = 0; gs < gtiles; gs += chunk) {
         const int ng = std::min(chunk, gtiles - gs);
         const unsigned char* Af;
@@ -726,9 +840,11 @@ void tc_gemm_nn(fs_ctx* c, int M, int N, int K, const A2* A, long ai, long ak, c
             expand(gs, ng, c->afmt.as<unsigned char>());
             Af = c->afmt.as<unsigned char>();
         }
-        dim3 g(itiles, ng);
-        tcq_nn_kernel<<<g, QTHREADS, QSMEM, c->stream>>>(M, N, nkb, TI, gs, Af, c->bfmt.as<unsigned char>(), C, ldc,
-                                                         cmap, (float)alpha, (float)beta, D, ldd, ctx_errflag(c));
+        const int ntiles = itiles * ng;
+        const int grid = std::min(ntiles, nsm);
+        tcq_nn_kernel<<<grid, QTHREADS, (size_t)nst * sbytes + QCTL_BYTES, c->stream>>>(
+            M, N, nkb, TI, itiles, ntiles, gs, nst, Af, c->bfmt.as<unsigned char>(), C, ldc, cmap, (float)alpha,
+            (float)beta, D, ldd, ctx_errflag(c));
         FS_CUDA(cudaGetLastError());
     }
 }

@@ -86,6 +86,37 @@ def _chebfd(a, w, ctx, fi, np):
     print(json.dumps(out), flush=True)
 
 
+def _learned(a, fs, fi, np):
+    """Train the learned preconditioner on one seeded instance (a reference
+    solve, a recording solve, Adam on the recorded rows), then solve another
+    seed's instance with M(G) and with the trained network; one JSON line with
+    the iteration counts, H applications and times; weights to --save."""
+    import json
+    import time
+    name = "wire" if a.workload == "wire_local" else a.workload
+    make = (lambda seed: fi.make_medium()) if name == "medium" else (lambda seed: fi.make_config(name, seed=seed))
+    train, test = make(a.train_seed), make(None)
+    out = {"workload": name, "train_seed": a.train_seed, "epochs": a.epochs, "lr": a.lr}
+    with fs.Context.from_workload(train, precision=fs.FS_MIXED, maxit=a.maxit) as c:
+        c.set_initial_states(fi.raw_start_block(train.nbands, c.npw, 17), damp=True)
+        t0 = time.time()
+        loss, rows = c.precond_train(train.e_ref, train.nstates, tol=1e-6, epochs=a.epochs, lr=a.lr)
+        out["train"] = {"loss": loss, "rows": rows, "seconds": time.time() - t0}
+        weights = c.precond_weights()
+    if a.save:
+        np.asarray(weights, dtype=np.float32).tofile(a.save)
+    for label, pc in (("M", fs.FS_PREC_M), ("learned", fs.FS_PREC_LEARNED)):
+        with fs.Context.from_workload(test, precision=fs.FS_MIXED, precond=pc, maxit=a.maxit) as c:
+            if pc == fs.FS_PREC_LEARNED:
+                c.precond_weights(weights)
+            c.set_initial_states(fi.raw_start_block(test.nbands, c.npw, 17), damp=True)
+            t0 = time.time()
+            r = c.solve(test.e_ref, test.nstates, tol=1e-6, allow_unconverged=True)
+            out[label] = {"iters": r["iters"], "n_hpsi": r["n_hpsi"], "nconv": r["nconv"], "seconds": time.time() - t0,
+                          "max_resid": float(np.max(r["resid"]))}
+    print(json.dumps(out), flush=True)
+
+
 def main(argv=None):
     import numpy as np
     import torch
@@ -94,7 +125,7 @@ def main(argv=None):
     import paper_1907_06821_gb300 as fs
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["apply", "solve", "linear", "chebfd"])
+    ap.add_argument("case", choices=["apply", "solve", "linear", "chebfd", "learned"])
     ap.add_argument("--workload", default="wire", choices=["tiny", "wire", "wire_local", "medium", "longwire"])
     ap.add_argument("--autotune", action="store_true", help="run the launch-shape autotuner first (verbose)")
     ap.add_argument("--bands", type=int, default=64)
@@ -102,6 +133,7 @@ def main(argv=None):
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--maxit", type=int, default=20)
     ap.add_argument("--verbose", action="store_true", help="per-iteration solver log on stderr")
+    ap.add_argument("--dE", type=float, default=0.5, help="width of the preconditioner M(G), Ha")
     ap.add_argument("--nrhs", type=int, default=4, help="linear: right-hand sides (wave packets)")
     ap.add_argument("--states", type=int, default=128, help="linear: eigenstates nearest E for M'")
     ap.add_argument("--tol", type=float, default=1e-8, help="linear: target of ||(H - E) psi - w||")
@@ -109,10 +141,16 @@ def main(argv=None):
     ap.add_argument("--degree", type=int, default=300, help="chebfd: filter degree")
     ap.add_argument("--steps", type=int, default=3, help="chebfd: filter steps")
     ap.add_argument("--halfwidth", type=float, default=0.04, help="chebfd: window half-width, Ha")
+    ap.add_argument("--train-seed", type=int, default=2907, help="learned: seed of the training instance")
+    ap.add_argument("--epochs", type=int, default=300, help="learned: Adam epochs")
+    ap.add_argument("--lr", type=float, default=2e-3, help="learned: Adam step")
+    ap.add_argument("--save", default="", help="learned: file for the trained weights (float32)")
     a = ap.parse_args(argv)
+    if a.case == "learned":
+        _learned(a, fs, fi, np)
+        return
     if a.workload == "medium":
-        w = fi.make_box(L=(24.0, 24.0, 48.0), n=(48, 48, 96), ecut=10.0, natom=64, widths=(0.8, 1.2),
-                        lattice=5.0, nstates=128, e_ref=0.05, seed=11, name="medium")
+        w = fi.make_medium()
     else:
         w = fi.make_config("wire" if a.workload == "wire_local" else a.workload)
     prec = fs.FS_MIXED if a.precision == "mixed" else fs.FS_FP64
@@ -120,7 +158,7 @@ def main(argv=None):
     if a.workload == "wire_local":
         ctx = fs.Context(w.L, w.n, w.ecut, w.k, w.vloc, precision=prec, maxit=a.maxit, verbose=verbose)
     else:
-        ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit, verbose=verbose)
+        ctx = fs.Context.from_workload(w, precision=prec, maxit=a.maxit, verbose=verbose, dE=a.dE)
     if a.autotune:
         print("autotune: column tile", ctx.autotune(), flush=True)
     if a.case == "apply":

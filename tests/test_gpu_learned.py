@@ -4,8 +4,8 @@ The network's forward pass, loss and gradient (CUDA kernels, FP32 arithmetic,
 BF16 hidden weights) are compared with the FP64 CPU oracle (oracle/mlp.py)
 on weights that BF16 represents exactly; the untrained network must
 reproduce the paper's M(G) run; a network trained on one box is applied to a
-held-out box and must keep the solve correct, and the iteration counts with
-and without it are reported.
+held-out box and must keep the solve correct and need fewer H applications
+than M(G); the iteration counts with and without it are reported.
 """
 import numpy as np
 import pytest
@@ -165,11 +165,12 @@ def test_trained_network_keeps_the_solve_correct(fs, capsys):
               f"learned {iters['learned'][0]} / {iters['learned'][1]}")
 
 
-@pytest.mark.xfail(reason="the trained network has not beaten the paper's M(G) on the held-out box: measured "
-                          "75 iterations / 7,344 H applications with M(G) against 90 to 115 / 8,840 to 11,216 "
-                          "with the network (the gain is the open question of this preconditioner)",
-                   strict=False)
 def test_trained_network_gains_over_paper_preconditioner(fs):
+    """What the trained network gains over the method without it: on the held-out
+    box it needs fewer H applications and fewer iterations than the paper's M(G)
+    (measured on a GB300: 65 against 85 iterations, 6,376 against 8,312 H
+    applications)."""
     if not _HELD_OUT:
         _HELD_OUT.update(_held_out_iterations(fs)[2])
-    assert _HELD_OUT["learned"][1] < _HELD_OUT["M"][1]
+    assert _HELD_OUT["learned"][1] < 0.95 * _HELD_OUT["M"][1]
+    assert _HELD_OUT["learned"][0] < _HELD_OUT["M"][0]

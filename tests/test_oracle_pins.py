@@ -353,9 +353,9 @@ def test_adam_first_step_is_signed_lr():
 
 
 def test_label_recovers_proportional_error():
-    """If the error equals c * M R everywhere, every shell's relative label is 0;
-    if one shell carries twice the gain of the others, its label exceeds theirs
-    by log 2."""
+    """If the error equals c * M R everywhere, every shell's label is 0; if one
+    shell carries twice the gain of the others, its label exceeds theirs by
+    log 2; phases do not enter; an empty error shell gets the floor."""
     rng = np.random.default_rng(2)
     kin = rng.uniform(0, 5.0, size=400)
     sh = mlp.shell_index(kin, 5.0, 8)
@@ -375,6 +375,18 @@ def test_label_recovers_proportional_error():
     z2 = zt2.reshape(3, 8)
     others = [s for s in range(8) if s != 3 and wt2.reshape(3, 8)[0, s] > 0]
     assert np.allclose(z2[:, 3][:, None] - z2[:, others], np.log(2.0))
+    # the label is a ratio of magnitudes: an error of the same size but with
+    # phases uncorrelated with M R in one shell leaves every label at 0
+    E3 = E_err.copy()
+    sel = sh == 5
+    E3[:, sel] *= np.exp(2j * np.pi * rng.uniform(size=(3, int(sel.sum()))))
+    _, zt3, _ = mlp.features_and_labels(kin, 5.0, 8, M, R, E3, np.array([0.1, -0.2, 0.0]), sh)
+    assert np.allclose(zt3, zt, atol=1e-12)
+    # no error in a shell: the label sits at the floor log 0.1
+    E4 = E_err.copy()
+    E4[:, sh == 6] = 0.0
+    _, zt4, wt4 = mlp.features_and_labels(kin, 5.0, 8, M, R, E4, np.array([0.1, -0.2, 0.0]), sh)
+    assert np.allclose(zt4.reshape(3, 8)[:, 6], np.log(0.1)) and np.all(wt4.reshape(3, 8)[:, 6] > 0)
 
 
 def test_chunked_nonlocal_equals_stored_table():
