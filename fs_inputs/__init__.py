@@ -235,14 +235,14 @@ def make_box(L=(10.0, 10.0, 20.0), n=(16, 16, 32), ecut=5.0, k=(0.0, 0.0, 0.0),
                    seed=seed, guard=guard)
 
 
-def make_medium() -> Workload:
+def make_medium(seed: int = 11) -> Workload:
     """The medium box: 24 x 24 x 48 bohr on a 48 x 48 x 96 grid at 20 Ry (41,657
     plane waves), 64 wells on a jittered simple-cubic lattice (a = 5), projectors
     of widths 0.8 and 1.2 (512 in all), the 128 states nearest 0.05 Ha.  Its band
     blocks exceed the L2 cache with about 2 GB on the device, and a plain FP64
     solve of it takes about a minute."""
     return make_box(L=(24.0, 24.0, 48.0), n=(48, 48, 96), ecut=10.0, natom=64, widths=(0.8, 1.2),
-                    lattice=5.0, nstates=128, e_ref=0.05, seed=11, name="medium")
+                    lattice=5.0, nstates=128, e_ref=0.05, seed=seed, name="medium")
 
 
 BATCH_GRIDS = ((32, 32, 32), (40, 40, 40), (48, 48, 48), (64, 64, 64), (48, 48, 96))

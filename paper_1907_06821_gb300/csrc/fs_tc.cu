@@ -515,18 +515,32 @@ tcq_nn_kernel(int M, int N, int nkb, int TI, int itiles, int ntiles, int gt0, in
             }
             if (!ok) break;
             if (g < N) {
+                // in groups of 8 outputs: the row indices, then the D values, then the
+                // stores, so that the loads of a group are in flight together (D may be
+                // C itself; each thread reads only the elements it writes)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int c0 = 128 * h + 32 * j;
+                    if (c0 >= ni) continue;  // warp-uniform
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int ii = c0 + e;
-                        if (ii < ni) {
-                            const long row = cmap ? (long)cmap[i0 + ii] : (long)(i0 + ii);
-                            float o = alpha * acc.v[j][e];
-                            if (beta != 0.f) o += beta * Df[(row * ldd + g) * 2 + comp];
-                            Cf[(row * ldc + g) * 2 + comp] = o;
+                    for (int e0 = 0; e0 < 32; e0 += 8) {
+                        long row[8];
+                        float dv[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int ii = c0 + e0 + e;
+                            row[e] = ii < ni ? (cmap ? (long)__ldg(cmap + i0 + ii) : (long)(i0 + ii)) : -1;
                         }
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            dv[e] = (beta != 0.f && row[e] >= 0) ? Df[(row[e] * ldd + g) * 2 + comp] : 0.f;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (row[e] >= 0) {
+                                float o = alpha * acc.v[j][e0 + e];
+                                if (beta != 0.f) o += beta * dv[e];
+                                Cf[(row[e] * ldc + g) * 2 + comp] = o;
+                            }
                     }
                 }
             }

@@ -94,7 +94,10 @@ def _learned(a, fs, fi, np):
     import json
     import time
     name = "wire" if a.workload == "wire_local" else a.workload
-    make = (lambda seed: fi.make_medium()) if name == "medium" else (lambda seed: fi.make_config(name, seed=seed))
+    if name == "medium":
+        make = lambda seed: fi.make_medium(11 if seed is None else seed)  # noqa: E731
+    else:
+        make = lambda seed: fi.make_config(name, seed=seed)  # noqa: E731
     train, test = make(a.train_seed), make(None)
     out = {"workload": name, "train_seed": a.train_seed, "epochs": a.epochs, "lr": a.lr}
     with fs.Context.from_workload(train, precision=fs.FS_MIXED, maxit=a.maxit) as c:
@@ -106,14 +109,15 @@ def _learned(a, fs, fi, np):
     if a.save:
         np.asarray(weights, dtype=np.float32).tofile(a.save)
     for label, pc in (("M", fs.FS_PREC_M), ("learned", fs.FS_PREC_LEARNED)):
-        with fs.Context.from_workload(test, precision=fs.FS_MIXED, precond=pc, maxit=a.maxit) as c:
+        with fs.Context.from_workload(test, precision=fs.FS_MIXED, precond=pc, maxit=a.maxit,
+                                      verbose=int(a.verbose)) as c:
             if pc == fs.FS_PREC_LEARNED:
                 c.precond_weights(weights)
             c.set_initial_states(fi.raw_start_block(test.nbands, c.npw, 17), damp=True)
             t0 = time.time()
             r = c.solve(test.e_ref, test.nstates, tol=1e-6, allow_unconverged=True)
-            out[label] = {"iters": r["iters"], "n_hpsi": r["n_hpsi"], "nconv": r["nconv"], "seconds": time.time() - t0,
-                          "max_resid": float(np.max(r["resid"]))}
+            out[label] = {"iters": r["iters"], "iters_mixed": r["iters_mixed"], "n_hpsi": r["n_hpsi"],
+                          "nconv": r["nconv"], "seconds": time.time() - t0, "max_resid": float(np.max(r["resid"]))}
     print(json.dumps(out), flush=True)
 
 
