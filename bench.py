@@ -40,6 +40,11 @@ import numpy as np  # noqa: E402
 NCU_TRAFFIC_RATIO = {
     "nonlocal_project": (426.996736e6 + 14.766592e6) / ((512 + 64) * 41657 * 8 + 512 * 64 * 16),
     "nonlocal_add": (706.371584e6 + 18.200576e6) / ((512 + 2 * 64) * 41657 * 8 + 64 * 512 * 16),
+    # the same ratio for a Gram matrix of two 136-band blocks and for the in-place projection
+    # W -= X (X^H W) of 136 bands, from the bounded medium solve (profiles/tcq_gram_kernel_medium_solve.md,
+    # profiles/tcq_nn_kernel_medium_solve.md): formatted images read once, tile re-reads from L2
+    "gram": (362.928896e6 + 10.022144e6) / ((136 + 136) * 41657 * 8 + 136 * 136 * 16),
+    "rotate": (227.311360e6 + 16.754176e6) / ((136 + 2 * 136) * 41657 * 8 + 136 * 136 * 16),
 }
 METRIC = "states converged/s to 1e-6 residual (mixed+learned vs plain FP64); Hψ HBM GB/s"
 TOL = 1e-6
@@ -356,7 +361,8 @@ def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, cloc
         roof = {"kernel": top, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": gbs / hbm, "traffic": traffic, "peak_source": f"{src} hbm_gbs"}
     roof["traffic_note"] = ("DRAM bytes per average launch: the ncu ratio of measured to algorithmic bytes "
-                            "(profiles/) times this run's algorithmic bytes per launch" if traffic else None)
+                            "on the medium box (profiles/) times this run's algorithmic bytes per launch (the wire "
+                            "launches are too large to capture)" if traffic else None)
     gemm_flops = sum(stats[k]["flops"] for k in ("gram", "rotate", "nonlocal_project", "nonlocal_add"))
     n_hpsi = sum(r["n_hpsi"] for r in results) / len(results)
     counts = {"n_hpsi": n_hpsi, "gemm_flops": gemm_flops / len(results)}
