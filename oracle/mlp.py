@@ -91,6 +91,25 @@ def forward(theta, F):
     return h[:, 0], acts
 
 
+def bf16_round(x):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((a + 0x7FFF + ((a >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(theta, F):
+    """The forward pass with the operands of the two 128 x 128 layers in BF16, as
+    an inference on tensor cores with BF16 inputs takes it: W2, W3 and the
+    activations that enter them (layers 1 and 2) rounded to BF16, W1 and W4
+    rounded to BF16, products accumulated and everything else in FP64."""
+    (W1, b1), (W2, b2), (W3, b3), (W4, b4) = unpack(theta)
+    h1 = np.tanh(F @ bf16_round(W1).T + b1)
+    h2 = np.tanh(bf16_round(h1) @ bf16_round(W2).T + b2)
+    h3 = np.tanh(bf16_round(h2) @ bf16_round(W3).T + b3)
+    return (h3 @ bf16_round(W4).T + b4)[:, 0]
+
+
 def loss_and_grad(theta, F, zt, wt):
     """Weighted MSE sum(w (z - z*)^2) / sum(w) and its gradient (backprop)."""
     z, acts = forward(theta, F)

@@ -4,8 +4,10 @@
 // with its forward pass, backward pass (weighted MSE on log-gain labels) and
 // Adam update as kernels here.  Parameter layout (flat FP32, master copy):
 //     W1[128][4] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[128] b4
-// The forward pass reads the hidden-layer weights rounded to BF16 (FP32
-// arithmetic); the master copy and the gradients stay FP32.
+// Training (forward and backward) reads the weights rounded to BF16 with FP32
+// arithmetic on CUDA cores; inference runs the two 128 x 128 layers on the tensor
+// cores with BF16 operands and FP32 accumulation; the master copy and the
+// gradients stay FP32.
 // Features: (shell centre / ecut, log10 shell share of |R|^2, d_i / 0.1 Ha,
 // log10 ||R_i|| / 10).  The output layer starts at zero, so the untrained
 // network is exactly the paper's M(G).
@@ -95,13 +97,212 @@ __device__ void mlp_tile_forward(const float* __restrict__ T, const float* __res
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(H) mlp_forward_kernel(const float* __restrict__ T, const float* __restrict__ F,
-                                                        int rows, float* __restrict__ z) {
-    __shared__ float h1[TR][H], h2[TR][H], h3[TR][H];
-    __shared__ float zsh[TR], red[TR * 4];
-    const int row0 = blockIdx.x * TR;
-    mlp_tile_forward(T, F, row0, rows, h1, h2, h3, zsh, red);
-    if (threadIdx.x < TR && row0 + threadIdx.x < rows) z[row0 + threadIdx.x] = zsh[threadIdx.x];
+// ------------------------------------------------------------------ tensor-core forward
+// Inference on the 5th-generation tensor cores: tiles of 128 rows, one thread per
+// row; layer 1 (K = 4) and layer 4 (N = 1) on CUDA cores, layers 2 and 3 as
+// tcgen05.mma kind::f16 with BF16 operands (the BF16 weights and the hidden
+// activations rounded to BF16) and FP32 accumulation in tensor memory (128 x 128).
+// Operands sit in shared memory in the K-major core-matrix layout (8 rows x 16 bytes
+// per core matrix, 16 core matrices along K); each MMA takes K = 16.
+constexpr int MT = 128;                               // rows per tile (UMMA M)
+constexpr int OP_BYTES = MT * H * 2;                  // one 128 x 128 BF16 operand (32 KB)
+constexpr int TC_SMEM = 3 * OP_BYTES + 64;            // W2, W3, activations, barrier + slot
+constexpr long long TC_WAIT_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, k) of a 128 x 128 BF16 K-major operand
+__device__ __forceinline__ uint32_t kmaj_bf16(int row, int k) {
+    return (uint32_t)((((row >> 3) * (H / 8) + (k >> 3)) << 7) + ((row & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint64_t sdesc_bf16(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;               // leading byte offset: next core matrix along K
+    d |= (uint64_t)(((H / 8) * 128) >> 4) << 32;   // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// kind::f16, BF16 A and B, FP32 D, K-major both, M = N = 128
+constexpr uint32_t IDESC_BF16 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                                ((uint32_t)(MT >> 4) << 24);
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_addr(bar);
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// the 8 MMAs of one layer: D = A W^T over K = 128, then a commit to bar
+__device__ __forceinline__ void tc_layer_mma(uint32_t tmem, uint32_t a, uint32_t w, uint64_t* bar) {
+#pragma unroll
+    for (int ks = 0; ks < H / 16; ++ks) {
+        const uint64_t ad = sdesc_bf16(a + ks * 256), bd = sdesc_bf16(w + ks * 256);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(tmem), "l"(ad), "l"(bd), "r"(IDESC_BF16), "r"(ks > 0 ? 1u : 0u));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 32 consecutive accumulator columns of this thread's row (lane quadrant of its warp)
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 8 BF16 values as one 16-byte chunk
+__device__ __forceinline__ uint4 pack8(const float* v) {
+    uint4 o;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&o);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * i]));
+        const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(v[2 * i + 1]));
+        w[i] = lo | (hi << 16);
+    }
+    return o;
+}
+
+// the activation row of this thread: tanh(accumulator + bias) into the A operand
+// (BF16), or, for the last hidden layer, dotted with W4 (FP32) into z
+__device__ __forceinline__ float tc_drain(uint32_t tmem, const float* __restrict__ bias, unsigned char* act,
+                                          const float* __restrict__ w4, int row) {
+    const int warp = threadIdx.x >> 5;
+    float zsum = 0.f;
+#pragma unroll
+    for (int c = 0; c < H / 32; ++c) {
+        float v[32];
+        tc_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * c), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = tanhf(v[i] + bias[32 * c + i]);
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                *reinterpret_cast<uint4*>(act + kmaj_bf16(row, 32 * c + 8 * q)) = pack8(v + 8 * q);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) zsum += w4[32 * c + i] * v[i];
+        }
+    }
+    return zsum;
+}
+
+__global__ void __launch_bounds__(MT, 1) mlp_forward_tc_kernel(const float* __restrict__ P,
+                                                              const float* __restrict__ T,
+                                                              const float* __restrict__ F, int rows,
+                                                              float* __restrict__ z, int* errflag) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* w2 = smem;
+    unsigned char* w3 = smem + OP_BYTES;
+    unsigned char* act = smem + 2 * OP_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 3 * OP_BYTES);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 3 * OP_BYTES + 8);
+    __shared__ float w1s[H * 4], b1s[H], b2s[H], b3s[H], w4s[H];
+    const int t = threadIdx.x;
+    // weights: W2, W3 (row n = output, K = input) as BF16 operands; the rest as the
+    // CUDA-core forward reads them (T: BF16-rounded W1 and W4, FP32 biases)
+    for (int e = t; e < H * H; e += MT) {
+        const int n = e / H, k = e % H;
+        *reinterpret_cast<__nv_bfloat16*>(w2 + kmaj_bf16(n, k)) = __float2bfloat16_rn(P[P_W2 + e]);
+        *reinterpret_cast<__nv_bfloat16*>(w3 + kmaj_bf16(n, k)) = __float2bfloat16_rn(P[P_W3 + e]);
+    }
+    for (int e = t; e < H * 4; e += MT) w1s[e] = T[P_W1 + e];
+    b1s[t] = T[P_B1 + t];
+    b2s[t] = T[P_B2 + t];
+    b3s[t] = T[P_B3 + t];
+    w4s[t] = T[P_W4 + t];
+    const float b4 = T[P_B4];
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (t < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"(H));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t a_s = smem_addr(act), w2_s = smem_addr(w2), w3_s = smem_addr(w3);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile * MT < rows && ok; tile += gridDim.x) {
+        const int row = tile * MT + t;
+        // layer 1 on CUDA cores, into the A operand (BF16)
+        float f[4] = {0.f, 0.f, 0.f, 0.f};
+        if (row < rows)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) f[k] = F[(long)row * 4 + k];
+#pragma unroll
+        for (int c = 0; c < H / 8; ++c) {
+            float v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int j = 8 * c + i;
+                float a = b1s[j];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a += w1s[k * H + j] * f[k];
+                v[i] = tanhf(a);
+            }
+            *reinterpret_cast<uint4*>(act + kmaj_bf16(t, 8 * c)) = pack8(v);
+        }
+        float zr = 0.f;
+#pragma unroll
+        for (int layer = 0; layer < 2; ++layer) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (t == 0) tc_layer_mma(tmem, a_s, layer == 0 ? w2_s : w3_s, bar);
+            // every thread polls; the vote keeps each warp together if one gives up
+            if (!__all_sync(0xffffffffu, tc_wait(bar, phase))) ok = false;
+            phase ^= 1;
+            if (!__syncthreads_and(ok)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (layer == 0)
+                tc_drain(tmem, b2s, act, nullptr, t);
+            else
+                zr = tc_drain(tmem, b3s, nullptr, w4s, t);
+        }
+        if (ok && row < rows) z[row] = b4 + zr;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (!ok && t == 0) atomicExch(errflag, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H));
 }
 
 // Loss sum_r w_r (z_r - t_r)^2 * inv_sw and its gradient, one partial per block.
@@ -423,7 +624,18 @@ void mlp_prepare(fs_ctx* c) {
 void mlp_forward(fs_ctx* c, const float* F, int rows, float* z) {
     if (rows <= 0) return;
     ProfScope ps(c, KS_VECTOR, rows * 20.0, rows * 2.0 * (4 * H + 2 * H * H + H));
-    mlp_forward_kernel<<<(rows + TR - 1) / TR, H, 0, c->stream>>>(c->mlp.T.as<float>(), F, rows, z);
+    static bool attr = false;
+    if (!attr) {
+        FS_CUDA(cudaFuncSetAttribute((const void*)mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TC_SMEM));
+        attr = true;
+    }
+    int dev = 0, nsm = 0;
+    FS_CUDA(cudaGetDevice(&dev));
+    FS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::max(1, std::min((rows + MT - 1) / MT, nsm));
+    mlp_forward_tc_kernel<<<grid, MT, TC_SMEM, c->stream>>>(c->mlp.P.as<float>(), c->mlp.T.as<float>(), F, rows, z,
+                                                            ctx_errflag(c));
     FS_CUDA(cudaGetLastError());
 }
 

@@ -1,8 +1,8 @@
 """Learned G-shell preconditioner on the GPU.
 
-The network's forward pass, loss and gradient (CUDA kernels, FP32 arithmetic,
-BF16 hidden weights) are compared with the FP64 CPU oracle (oracle/mlp.py)
-on weights that BF16 represents exactly; the untrained network must
+The network's inference (tensor cores, BF16 operands, FP32 accumulation), loss
+and gradient (CUDA cores, FP32 arithmetic, BF16 weights) are compared with the
+FP64 CPU oracle (oracle/mlp.py) on weights that BF16 represents exactly; the untrained network must
 reproduce the paper's M(G) run; a network trained on one box is applied to a
 held-out box and must keep the solve correct and need fewer H applications
 than M(G); the iteration counts with and without it are reported.
@@ -39,16 +39,28 @@ def random_weights(seed):
     return bf16_exact(th.astype(np.float32))
 
 
-def test_forward_matches_oracle(fs):
+@pytest.mark.parametrize("rows", [1000, 25001])      # 8 tiles with a ragged tail; more tiles than SMs
+def test_forward_matches_oracle(fs, rows):
+    """Inference (tensor cores, BF16 operands of the 128 x 128 layers, FP32
+    accumulation) against the oracle's forward with the same BF16 roundings.
+    Tolerance: an activation whose FP32 value lies within FP32 rounding of a BF16
+    rounding boundary may round to the neighbouring BF16 value on one side
+    (2^-8 relative, about 3e-5 of the activations); its effect on z stays below
+    5e-3.  Against the unrounded FP64 forward (the form training uses) the
+    tensor-core result stays within 5e-2, the effect of the BF16 activations."""
     w = fi.make_config("tiny")
     with fs.Context.from_workload(w) as c:
         th = random_weights(4)
         c.precond_weights(th)
         assert np.array_equal(c.precond_weights(), th)
-        F = np.random.default_rng(1).normal(size=(1000, 4)).astype(np.float32)
+        F = np.random.default_rng(1).normal(size=(rows, 4)).astype(np.float32)
         z = c.precond_eval(torch.from_numpy(F).cuda()).cpu().numpy()
-        zo, _ = mlp.forward(th.astype(np.float64), F.astype(np.float64))
-        assert np.abs(z - zo).max() <= 1e-4 * max(1.0, np.abs(zo).max())
+        zo = mlp.forward_bf16(th.astype(np.float64), F.astype(np.float64))
+        scale = max(1.0, np.abs(zo).max())
+        assert np.abs(z - zo).max() <= 5e-3 * scale
+        assert np.median(np.abs(z - zo)) <= 1e-5 * scale     # almost every row to FP32 accuracy
+        zf, _ = mlp.forward(th.astype(np.float64), F.astype(np.float64))
+        assert np.abs(z - zf).max() <= 5e-2 * scale
 
 
 def test_loss_and_gradient_match_oracle(fs):

@@ -400,3 +400,23 @@ def test_chunked_nonlocal_equals_stored_table():
     X = fi.raw_start_block(5, h.npw, 2)
     a, b = h.apply(X, 0.1), hc.apply(X, 0.1)
     assert np.abs(a - b).max() <= 1e-13 * np.abs(a).max()
+
+
+def test_bf16_rounding_and_forward():
+    """bf16_round: nearest BF16 with ties to even (closed-form cases); the BF16
+    forward of the tensor-core inference equals the FP64 forward when no
+    rounding happens (zero output layer) and stays within the BF16 error bound
+    otherwise."""
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -(1.0 + 2.0 ** -7), 2.0 ** -130, 3.0])
+    want = np.array([1.0, 1.0, 1.0 + 2.0 ** -7, -(1.0 + 2.0 ** -7), 2.0 ** -130, 3.0])
+    assert np.array_equal(mlp.bf16_round(x), want)
+    v = np.random.default_rng(5).normal(size=1000)
+    r = mlp.bf16_round(v)
+    assert np.array_equal(mlp.bf16_round(r), r)
+    assert np.all(np.abs(r - v) <= 2.0 ** -8 * np.abs(v) * (1 + 1e-6))        # half a BF16 spacing
+    th = mlp.init_params(3)
+    F = np.random.default_rng(6).normal(size=(200, 4))
+    assert np.array_equal(mlp.forward_bf16(th, F), mlp.forward(th, F)[0])     # output layer zero
+    th = th + 0.1 * np.random.default_rng(7).normal(size=th.size)
+    zb, z = mlp.forward_bf16(th, F), mlp.forward(th, F)[0]
+    assert 0 < np.abs(zb - z).max() <= 5e-2 * max(1.0, np.abs(z).max())
