@@ -321,7 +321,7 @@ def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, cloc
     hpsi = ("col_inverse_fft", "plane_fft_vloc", "col_forward_fft")
     hpsi_ms = sum(stats[k]["ms"] for k in hpsi)
     hpsi_bytes = sum(stats[k]["bytes"] for k in hpsi)
-    # the survey's algorithmic bytes of one band application of the local term (FP32): sphere in
+    # the algorithmic bytes of one band application of the local term (FP32): sphere in
     # and out, two 3-D FFTs of two grid passes each (read + write of the full grid)
     ng = int(np.prod(w.n))
     hpsi_alg_band = 2.0 * ctx.npw * 8 + 2 * 2 * 2 * ng * 8.0
@@ -387,10 +387,10 @@ def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, cloc
         "roofline": roof,
         "hpsi_gbs": hpsi_bytes / (hpsi_ms / 1e3) / 1e9 if hpsi_ms > 0 else None,
         "hpsi_frac_hbm": (hpsi_bytes / (hpsi_ms / 1e3) / 1e9) / hbm if hpsi_ms > 0 else None,
-        "hpsi_survey": {"bytes_per_band": hpsi_alg_band, "bands": hpsi_bands,
+        "hpsi_algorithmic": {"bytes_per_band": hpsi_alg_band, "bands": hpsi_bands,
                         "GB/s": hpsi_alg_band * hpsi_bands / (hpsi_ms / 1e3) / 1e9 if hpsi_ms > 0 else None,
                         "frac_hbm": hpsi_alg_band * hpsi_bands / (hpsi_ms / 1e3) / 1e9 / hbm if hpsi_ms > 0 else None,
-                        "note": "the survey's algorithmic bytes of the local term per band (sphere in and out, "
+                        "note": "algorithmic bytes of the local term per band (sphere in and out, "
                                 "2 FFTs x 2 grid passes x read+write of the full grid, FP32) over the event time "
                                 "of the three FFT kernels"},
         "kernel_time_share": {k: round(v["ms"] / total_ms, 4) for k, v in stats.items() if total_ms > 0},

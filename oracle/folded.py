@@ -22,7 +22,7 @@ Everything is FP64 with plain NumPy/SciPy calls; no blocking or fusion.
 This module is a fixed reference algorithm: it does not follow the tuning of
 the CUDA solver (its locking, stall and precision rules), and a change to it
 must be justified by the paper's text or by the mathematics alone.  The
-judge of every solver result is the plain definition (the eigenpairs of H
+arbiter of every solver result is the plain definition (the eigenpairs of H
 nearest E by LAPACK brute force, or the golden spectrum of the wire), not
 agreement with the iterations of this module.
 """

@@ -56,7 +56,7 @@ def test_gpu_arm_line_assembly():
     assert roof["traffic"] is not None                          # an ncu ratio exists for this kernel
     assert d["e2e"]["h2d_bytes_per_step"] == 272 * 10 * 16
     assert d["gpu_launches"] == sum(v["launches"] for v in stats.values())
-    hs = d["hpsi_survey"]
+    hs = d["hpsi_algorithmic"]
     bands = stats["col_inverse_fft"]["bytes"] / ((193673 + 144 * 57 * 45) * 8.0)
     assert abs(hs["bands"] - bands) <= 1e-9 * bands
     assert hs["bytes_per_band"] == 2 * 193673 * 8 + 8 * 72 * 72 * 144 * 8

@@ -1,5 +1,5 @@
 """Parity of the folded-spectrum linear solve (Sec. II.C, Eq. wl1 with the M'
-preconditioner) through the C ABI with the CPU FP64 oracle.  The judge of the
+preconditioner) through the C ABI with the CPU FP64 oracle.  What decides the
 result is the spectral expansion of the solution over every eigenpair of the
 dense H (LAPACK); the eigenstate preconditioner built from the library's own
 eigensolve must cut the iteration count.  The oracle's PCG iteration counts
