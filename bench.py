@@ -174,7 +174,7 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": res["desc"], "precision": "fp64 (oracle)", "tol": TOL, "sample": res["sample"]},
             "cpu_baseline": {"value": res["value"], "unit": "states/s", "cores": res["cores"],
-                             "kind": "oracle", "sample": res["sample"]},
+                             "kind": "oracle", "sample": res["sample"], "tiny_full_solve": res["tiny_full_solve"]},
             "e2e": {"value": res["value"], "unit": "states/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -213,7 +213,25 @@ def cpu_baseline(name, gpu_counts):
     value = w.nstates / est
     sample = (f"extrapolated: oracle H on {nb} bands ({t_h * 1e3:.1f} ms/band) and one {m}x{m} Gram product over "
               f"{h.npw} plane waves ({t_gram:.2f} s), {how}; setup {t_setup:.1f} s")
-    return dict(value=value, cores=cores, sample=sample, seconds_per_solve=est, desc=workload_desc(name, w, h.npw))
+    return dict(value=value, cores=cores, sample=sample, seconds_per_solve=est, desc=workload_desc(name, w, h.npw),
+                tiny_full_solve=oracle_tiny_solve())
+
+
+def oracle_tiny_solve():
+    """A complete oracle solve (FP64 block PCG) of the tiny workload, measured: the
+    one configuration where the CPU solve runs to convergence in seconds."""
+    import fs_inputs as fi
+    from oracle import folded as fo
+    from oracle import planewave as pw
+    w = fi.make_config("tiny")
+    h = pw.Hamiltonian(w)
+    x0 = fi.raw_start_block(w.nbands, h.npw, 17)
+    t0 = time.time()
+    r = fo.solve_folded(w, w.e_ref, w.nstates, TOL, x0, ham=h)
+    dt = time.time() - t0
+    n = int(np.sum(np.asarray(r["resid"]) <= TOL))
+    return {"value": n / dt, "unit": "states/s", "seconds": dt, "iters": int(r["iters"]), "nconv": n,
+            "kind": "measured", "workload": "tiny: grid (16, 16, 32), 1069 PWs, 8 states nearest 0.3 Ha"}
 
 
 def workload_desc(name, w, npw):
@@ -369,7 +387,8 @@ def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, cloc
     cpu = None
     if not args.no_cpu and ws == 1:
         c = cpu_baseline(args.workload, counts)
-        cpu = {"value": c["value"], "unit": "states/s", "cores": c["cores"], "kind": "oracle", "sample": c["sample"]}
+        cpu = {"value": c["value"], "unit": "states/s", "cores": c["cores"], "kind": "oracle", "sample": c["sample"],
+               "tiny_full_solve": c["tiny_full_solve"]}
     total_ms = sum(v["ms"] for v in stats.values())
     fp64 = None
     if fp32 and ws == 1 and getattr(args, "fp64_full", False):

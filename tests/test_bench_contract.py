@@ -26,6 +26,8 @@ def test_reference_arm_prints_one_contract_line():
     assert BASE_KEYS <= set(d) and d["impl"] == "reference"
     assert d["value"] > 0 and d["unit"] == "states/s" and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    tf = d["cpu_baseline"]["tiny_full_solve"]                   # a complete oracle solve, measured
+    assert tf["kind"] == "measured" and tf["nconv"] == 8 and tf["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "tiny" in d["config"]["workload"]
 
