@@ -156,6 +156,7 @@ fs_status fs_precond_eval(fs_ctx* c, const float* features, int rows, float* z) 
         mlp_setup(c);
         mlp_forward(c, features, rows, z);
         FS_CUDA(cudaStreamSynchronize(c->stream));
+        ctx_check_errflag(c);  // a bounded wait of the tensor-core forward that gave up
     });
 }
 
