@@ -347,9 +347,9 @@ def make_line(args, w, ctx, results, stats, nconv, tmax, t_e2e, e2e_states, cloc
     g = ctx.gvectors()
     ncol = len(np.unique(np.asarray(g)[:, 0] * 100003 + np.asarray(g)[:, 1]))
     hpsi_bands = stats["col_inverse_fft"]["bytes"] / ((ctx.npw + w.n[2] * ncol) * 8.0)
-    # roofline of the library's own dominant kernel class in the FP32 stage (the FP64 dense
-    # eigensolves are cuSOLVER calls and the FP64 classes are the final check; their shares are
-    # reported in kernel_time_share)
+    # roofline of the library's dominant GEMM / FFT / vector class in the FP32 stage (the FP64
+    # dense algebra is latency- and FP64-bound, and the FP64 classes are the final check; their
+    # shares are reported in kernel_time_share and dense_la_parts)
     own = {k: v for k, v in stats.items()
            if k not in ("dense_la", "nonlocal_D") and not k.endswith("_fp64") and v["ms"] > 0}
     top = max(own, key=lambda k: own[k]["ms"])

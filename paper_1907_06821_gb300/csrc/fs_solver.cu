@@ -221,7 +221,7 @@ struct Solver {
     // span of the directions before it) is below piv_floor, refactorising
     // without them; should that not settle, the basis comes from an
     // eigendecomposition of GB, dropping eigenvalues below tau * max.  Returns
-    // the cuSOLVER info (0 = success).
+    // the factorisation info (0 = success, else the failing column + 1).
     int rr_basis(int nb, bool robust, double tau, double piv_floor) {
         double2* GA = s.GA.as<double2>();
         double2* GB = s.GB.as<double2>();
